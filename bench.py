@@ -1,0 +1,418 @@
+"""Benchmark of the px hot path: hash exchange -> per-partition hash join ->
+Partial/Final hash aggregation, on the at-scale workload (60M-row fact with
+Zipf(1.1) keys over a 2M-row dimension, 64 partitions, group-by on a 10k-valued
+attribute), one step = one full pass of the pipeline over the batch.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl px|reference]
+
+Prints ONE JSON line (rank 0). `value` is whole-job fact rows per second with the
+inputs resident in HBM; `e2e` is the same metric through the same public calls
+with host inputs copied in (pinned memory) and the final groups copied out every
+step. `operators` breaks the step down per C-ABI call (rows/s and fraction of the
+measured HBM copy bandwidth on algorithmic bytes). `roofline` is the dominant
+call, the fact-side exchange (px_partition: histogram + scan + scatter kernels).
+`cpu_baseline` is the CPU oracle timed on this host on a bounded sample.
+
+`--impl reference` times the CPU oracle (the only reference implementation of
+this path) on the same workload and metric, on bounded samples per step.
+
+With N > 1 (torchrun, one process per GPU) every rank runs an independent replica
+on its own seeded shard of fact rows (weak scaling, no data-path collective);
+ranks meet only at the timing barriers and the max-over-ranks reduction.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import pxdata  # noqa: E402
+
+METRIC = "rows/s & % HBM peak per operator; served QPS + p50/p99 vs one-at-a-time"
+WORKLOAD = ("plain at scale: 60M-row fact (fk Zipf s=1.1 over 2M pks, amount int64, date int32) x 2M-row dim "
+            "(pk int64, attr int32 over 10k values); exchange both sides into 64 partitions, per-partition "
+            "join build+probe, Partial group-by attr per partition, Final merge")
+NFACT, NDIM, NATTR, NPARTS = 60_000_000, 2_000_000, 10_000, 64
+
+# Algorithmic bytes per unit of each call (measurement section).
+#   partition: read every column + write every column       (fact 20+20 B/row, dim 12+12 B/row)
+#   build:     read the key + write the 2 table slots per row (8 + 32 B/dim row)
+#   probe:     read fk + amount, write amount + attr          (16 + 12 B/fact row)
+#   partial:   read amount + attr                             (12 B/joined row)
+#   final:     read attr + 2 partial aggregates                (20 B/partial group)
+
+
+def alg_bytes(nf, nd, npartial):
+    return {
+        "px_partition(dim)": 24 * nd,
+        "px_partition(fact)": 40 * nf,
+        "px_join_build": 40 * nd,
+        "px_join_probe": 28 * nf,
+        "px_groupby_agg(partial)": 12 * nf,
+        "px_groupby_agg(final)": 20 * npartial,
+    }
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def shard_seed(rank: int) -> int:
+    """Seed of a rank's fact shard: rank 0 draws the single-GPU workload itself."""
+    return 3 + 1000 * rank
+
+
+def reduce_max(value: float, group=None) -> float:
+    """Max over ranks of a host float (timing only; no data-path collective)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return value
+    dev = "cuda" if dist.get_backend(group) == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX, group=group)
+    return float(t.item())
+
+
+def whole_job_rate(rows_per_rank: int, world: int, seconds_max: float) -> float:
+    """Units all ranks processed / the slowest rank's time."""
+    return rows_per_rank * world / seconds_max
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=5)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def ncu_traffic(kernel_src: str):
+    """DRAM bytes per launch of the dominant call from the committed ncu summary, or
+    None once the kernel source has changed since the counters were taken."""
+    p = os.path.join(ROOT, "profiles", "roofline_traffic.json")
+    if not os.path.exists(p):
+        return None, None
+    with open(p) as f:
+        d = json.load(f)
+    src = os.path.join(ROOT, kernel_src)
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    if d.get("source_sha256_16") != h:
+        return None, d.get("source_sha256_16")
+    return d.get("traffic_bytes_per_launch"), h
+
+
+# ---------------------------------------------------------------- oracle ----
+
+def oracle_rate(d: dict, nsample: int) -> tuple[float, str]:
+    """The CPU oracle (single-threaded, as it stands) on the first `nsample` fact rows
+    with the whole dimension: returns (fact rows/s, description)."""
+    import oracle
+    s = {"pk": d["pk"], "attr": d["attr"], "fk": d["fk"][:nsample], "amount": d["amount"][:nsample],
+         "date": d["date"][:nsample]}
+    t0 = time.perf_counter()
+    oracle.pipeline_at_scale(s, NPARTS)
+    dt = time.perf_counter() - t0
+    return nsample / dt, f"first {nsample} fact rows x full {d['pk'].size}-row dim, {dt:.1f} s"
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    d = pxdata.plain_at_scale(seed=shard_seed(0))
+    # size each step's sample so the whole run stays within ~2 minutes
+    probe_rate, _ = oracle_rate(d, 200_000)
+    per_step_s = min(10.0, 120.0 / max(1, args.steps + args.warmup))
+    nsample = int(min(NFACT, max(100_000, probe_rate * per_step_s * 0.8)))
+    for _ in range(args.warmup):
+        oracle_rate(d, nsample)
+    rates, desc = [], ""
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        r, desc = oracle_rate(d, nsample)
+        rates.append(r)
+    total = time.perf_counter() - t0
+    value = nsample * args.steps / total
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "rows/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+            "data": "synthetic (seeded numpy PCG64; TPC-H-like shapes, no TPC-H data)",
+            "config": {"workload": WORKLOAD, "fact_rows": NFACT, "dim_rows": NDIM, "nparts": NPARTS,
+                       "reference": "CPU oracle (plain single-threaded C++: stable-sort partition, sorted-build "
+                                    "join, ordered-map group-by), bounded sample per step"},
+            "cpu_baseline": {"value": value, "unit": "rows/s", "cores": 1, "kind": "oracle",
+                             "sample": f"per step: {desc.split(',')[0]}"},
+            "e2e": {"value": value, "unit": "rows/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# -------------------------------------------------------------------- px ----
+
+def run_px(args):
+    import torch
+    import torch.distributed as dist
+
+    import paper_2606_24647_gb300 as px
+    from paper_2606_24647_gb300.pipelines import AtScalePipeline
+
+    world, rank, local = dist_env()
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    px.load()
+    dev = torch.device("cuda", torch.cuda.current_device())
+
+    d = pxdata.plain_at_scale(seed=shard_seed(rank))
+    host = {k: torch.from_numpy(v).pin_memory() for k, v in d.items()}
+    dd = {k: v.to(dev, non_blocking=True) for k, v in host.items()}
+    torch.cuda.synchronize()
+    pipe = AtScalePipeline(dd, nparts=NPARTS, nattr_bound=NATTR)
+    stream = torch.cuda.current_stream()
+
+    ops = list(alg_bytes(1, 1, 1).keys())
+
+    def step(ev=None):
+        """One pass of the pipeline; ev: list of 7 events recorded between the calls."""
+        P, ws = pipe.nparts, pipe.ws
+        if ev:
+            ev[0].record(stream)
+        px.px_partition(pipe.dim, 0, P, pipe.seed, out=pipe.dparts, offsets=pipe.doff, ws=ws, stream=stream)
+        if ev:
+            ev[1].record(stream)
+        px.px_partition(pipe.fact, 0, P, pipe.seed, out=pipe.fparts, offsets=pipe.foff, ws=ws, stream=stream)
+        if ev:
+            ev[2].record(stream)
+        px.px_join_build(pipe.dparts, 0, seg=pipe.doff, unique=True, table=pipe.table, ws=ws, stream=stream)
+        if ev:
+            ev[3].record(stream)
+        j = px.px_join_probe(pipe.table, pipe.fparts, 0, seg=pipe.foff, carry=[1], payload=[pipe.dparts[1]],
+                             out=pipe.jout, out_cap=pipe.jout[0].numel(), out_seg=True, ws=ws, stream=stream)
+        if ev:
+            ev[4].record(stream)
+        part = px.px_groupby_agg(pipe.jout, [1], [(px.PX_SUM, 0, None), (px.PX_COUNT, None, None)],
+                                 max_groups=pipe.max_partial, seg=j["out_seg"], d_nrows=j["nout"], out=pipe.pout,
+                                 ws=ws, stream=stream)
+        if ev:
+            ev[5].record(stream)
+        fin = px.px_groupby_agg(pipe.pout, [0], [(px.PX_SUM, 1, None), (px.PX_SUM, 2, None)],
+                                max_groups=pipe.max_final, d_nrows=part["ngroups"], out=pipe.fout, ws=ws,
+                                stream=stream)
+        if ev:
+            ev[6].record(stream)
+        return part, fin
+
+    # correctness gate on this exact configuration before timing
+    part, fin = step()
+    st = pipe.ws.status(stream)
+    if st != px.PX_OK:
+        raise RuntimeError(f"device status {st} in the benchmarked pipeline")
+    npartial = int(part["ngroups"].item())
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    # ---- timed region: K steps, per-call events, inputs (1.2 GB) larger than L2 ----
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(7)] for _ in range(args.steps)]
+    clocks = ClockSampler(torch.cuda.current_device())
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.15)
+    launches0 = px.kernel_launches()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    for k in range(args.steps):
+        step(evs[k])
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    launches = px.kernel_launches() - launches0
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    total_ms = t_start.elapsed_time(t_end)
+    if pipe.ws.status(stream) != px.PX_OK:
+        raise RuntimeError("device status set during the timed region")
+
+    per_op_ms = {op: 0.0 for op in ops}
+    for k in range(args.steps):
+        for i, op in enumerate(ops):
+            per_op_ms[op] += evs[k][i].elapsed_time(evs[k][i + 1])
+    for op in ops:
+        per_op_ms[op] /= args.steps
+    max_total_s = reduce_max(total_ms / 1000.0)
+    ms_per_step = 1000 * max_total_s / args.steps
+    value = whole_job_rate(NFACT * args.steps, world, max_total_s)
+
+    peak, peak_kind = measured_peaks()
+    ab = alg_bytes(NFACT, NDIM, npartial)
+    rows = {"px_partition(dim)": NDIM, "px_partition(fact)": NFACT, "px_join_build": NDIM, "px_join_probe": NFACT,
+            "px_groupby_agg(partial)": NFACT, "px_groupby_agg(final)": npartial}
+    operators = {}
+    for op in ops:
+        s = per_op_ms[op] / 1000
+        gbs = ab[op] / s / 1e9
+        operators[op] = {"ms": round(per_op_ms[op], 4), "rows_per_s": rows[op] / s, "alg_bytes": ab[op],
+                         "GBps": round(gbs, 1), "hbm_frac": round(gbs / peak, 4)}
+    dom = "px_partition(fact)"
+    traffic, _ = ncu_traffic("paper_2606_24647_gb300/csrc/px_partition.cu")
+    dom_gbs = ab[dom] / (per_op_ms[dom] / 1000) / 1e9
+    roofline = {"bound": "hbm", "achieved": round(dom_gbs, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(dom_gbs / peak, 4), "traffic": traffic,
+                "kernel": "px_partition on the 60M-row fact (hist + scan + scatter kernels, one C-ABI call)",
+                "alg_bytes_per_launch": ab[dom], "peak_kind": f"{peak_kind} HBM copy bandwidth (burst)"}
+
+    # ---- end to end through the same public calls, host buffers in and out ----
+    e2e_steps = max(3, min(20, args.steps // 10))
+    out_host = {"keys": torch.empty(pipe.max_final, dtype=torch.int32).pin_memory(),
+                "sum": torch.empty(pipe.max_final, dtype=torch.int64).pin_memory(),
+                "cnt": torch.empty(pipe.max_final, dtype=torch.int64).pin_memory(),
+                "n": torch.empty(1, dtype=torch.int64).pin_memory()}
+    h2d = sum(v.numel() * v.element_size() for v in host.values())
+    d2h = sum(v.numel() * v.element_size() for v in out_host.values())
+
+    def e2e_step():
+        for k, v in host.items():
+            dd[k].copy_(v, non_blocking=True)
+        _, f = step()
+        out_host["keys"].copy_(f["keys"][0], non_blocking=True)
+        out_host["sum"].copy_(f["aggs"][0], non_blocking=True)
+        out_host["cnt"].copy_(f["aggs"][1], non_blocking=True)
+        out_host["n"].copy_(f["ngroups"], non_blocking=True)
+
+    e2e_step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(e2e_steps):
+        e2e_step()
+    b.record(stream)
+    torch.cuda.synchronize()
+    e2e_s = reduce_max(a.elapsed_time(b) / 1000.0)
+    e2e_value = whole_job_rate(NFACT * e2e_steps, world, e2e_s)
+    if pipe.ws.status(stream) != px.PX_OK:
+        raise RuntimeError("device status set during the end-to-end run")
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        rate, desc = oracle_rate(d, min(NFACT, args.cpu_sample))
+        cpu = {"value": rate, "unit": "rows/s", "cores": 1, "kind": "oracle", "sample": desc}
+
+    line = {"metric": METRIC, "value": value, "unit": "rows/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+            "data": "synthetic (seeded numpy PCG64; TPC-H-like shapes, no TPC-H data)",
+            "config": {"workload": WORKLOAD, "fact_rows": NFACT, "dim_rows": NDIM, "nparts": NPARTS,
+                       "attr_values": NATTR, "zipf_s": 1.1, "per_gpu_fact_rows": NFACT,
+                       "l2": "inputs larger than L2 (1.22 GB of fact+dim columns per step vs 129 MB L2)",
+                       "parallelism": f"replicas x{world} (independent seeded shards)"},
+            "operators": operators, "roofline": roofline, "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": "rows/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "steps": e2e_steps},
+            "gpu_launches": launches, "clocks": clk}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="px", choices=["px", "reference"])
+    ap.add_argument("--cpu-sample", type=int, default=6_000_000,
+                    help="fact rows of the oracle's CPU-baseline sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_px(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,327 @@
+"""px: GB300-native hash exchange, hash join and hash aggregation.
+
+Thin ctypes binding of the C ABI in include/px.h (libpx.so, built in-tree by
+``paper_2606_24647_gb300.build``). The functions here only marshal arguments:
+torch CUDA tensors in, raw device pointers and the caller's CUDA stream out to
+the library; every step of the operators runs in the library's CUDA kernels.
+There is no CPU fallback: if libpx.so cannot be loaded, or a tensor is not on a
+CUDA device, the call raises.
+
+PyTorch is used for device memory (outputs and workspaces are torch tensors) and
+streams (``torch.cuda.current_stream()`` unless one is passed).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libpx.so")
+
+PX_OK, PX_ERR_INVALID, PX_ERR_CAPACITY, PX_ERR_DUPLICATE_KEY = 0, 1, 2, 3
+PX_ERR_TABLE_FULL, PX_ERR_TIMEOUT, PX_ERR_CUDA, PX_ERR_UNSUPPORTED = 4, 5, 6, 7
+STATUS_NAMES = {0: "PX_OK", 1: "PX_ERR_INVALID", 2: "PX_ERR_CAPACITY", 3: "PX_ERR_DUPLICATE_KEY",
+                4: "PX_ERR_TABLE_FULL", 5: "PX_ERR_TIMEOUT", 6: "PX_ERR_CUDA", 7: "PX_ERR_UNSUPPORTED"}
+PX_I8, PX_I32, PX_I64 = 1, 4, 8
+PX_COUNT, PX_SUM, PX_SUM_MUL = 0, 1, 2
+
+EXPORTED = [
+    "px_ws_init", "px_stream_status", "px_last_error", "px_kernel_launches",
+    "px_filter_ws_bytes", "px_filter",
+    "px_partition_ws_bytes", "px_partition",
+    "px_join_table_bytes", "px_join_build_ws_bytes", "px_join_build",
+    "px_join_probe_ws_bytes", "px_join_probe",
+    "px_groupby_ws_bytes", "px_groupby_agg",
+]
+
+_TYPES = {torch.int8: PX_I8, torch.int32: PX_I32, torch.int64: PX_I64}
+
+
+class PxError(RuntimeError):
+    def __init__(self, status: int, where: str, message: str = ""):
+        self.status = status
+        super().__init__(f"{where}: {STATUS_NAMES.get(status, status)} {message}".strip())
+
+
+class px_col(ctypes.Structure):
+    _fields_ = [("type", ctypes.c_int32), ("reserved", ctypes.c_int32), ("data", ctypes.c_void_p)]
+
+
+class px_batch(ctypes.Structure):
+    _fields_ = [("ncols", ctypes.c_int32), ("reserved", ctypes.c_int32), ("cols", ctypes.POINTER(px_col)),
+                ("nrows", ctypes.c_int64), ("d_nrows", ctypes.c_void_p)]
+
+
+class px_agg(ctypes.Structure):
+    _fields_ = [("op", ctypes.c_int32), ("a", ctypes.c_int32), ("b", ctypes.c_int32)]
+
+
+_lib = None
+
+
+def _declare(lib):
+    P, I32, I64, U64, SZ = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, ctypes.c_size_t
+    BP = ctypes.POINTER(px_batch)
+    CP = ctypes.POINTER(px_col)
+    AP = ctypes.POINTER(px_agg)
+    sig = {
+        "px_ws_init": ([P, SZ, P], I32),
+        "px_stream_status": ([P, P], I32),
+        "px_last_error": ([], ctypes.c_char_p),
+        "px_kernel_launches": ([], U64),
+        "px_filter_ws_bytes": ([I64], SZ),
+        "px_filter": ([CP, I64, P, I64, I64, P, P, P, SZ, P], I32),
+        "px_partition_ws_bytes": ([I64, I32], SZ),
+        "px_partition": ([BP, I32, P, P, I32, U64, BP, P, P, SZ, P], I32),
+        "px_join_table_bytes": ([I64, I32], SZ),
+        "px_join_build_ws_bytes": ([I64], SZ),
+        "px_join_build": ([BP, I32, P, I32, I32, P, SZ, P, SZ, P], I32),
+        "px_join_probe_ws_bytes": ([I64], SZ),
+        "px_join_probe": ([P, BP, I32, P, P, P, I32, P, I32, BP, BP, P, P, P, P, P, SZ, P], I32),
+        "px_groupby_ws_bytes": ([I64, I64], SZ),
+        "px_groupby_agg": ([BP, P, I32, AP, I32, P, P, P, I32, I64, BP, P, P, P, SZ, P], I32),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+
+
+def load(path: str | None = None):
+    """Load libpx.so (building it first if its sources are newer). Raises if it is missing."""
+    global _lib
+    if _lib is None:
+        from . import build as _build
+        if path is None:
+            if _build.stale() and os.path.exists(_build.NVCC):
+                _build.build()
+            path = LIB_PATH
+        if not os.path.exists(path):
+            raise RuntimeError(f"px CUDA library not found at {path}; run paper_2606_24647_gb300.build.build()")
+        lib = ctypes.CDLL(path)
+        _declare(lib)
+        _lib = lib
+    return _lib
+
+
+def lib():
+    return load()
+
+
+def last_error() -> str:
+    return (load().px_last_error() or b"").decode()
+
+
+def kernel_launches() -> int:
+    """Kernels launched by libpx.so in this process so far."""
+    return int(load().px_kernel_launches())
+
+
+def _check(status: int, where: str):
+    if status != PX_OK:
+        raise PxError(status, where, last_error())
+
+
+def _ptr(t) -> int | None:
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("px tensors must be CUDA tensors")
+    return t.data_ptr()
+
+
+def _sel_ptr(sel) -> int | None:
+    """Device pointer of a selection vector; an empty one (null data in torch) is
+    replaced by a one-element buffer, its device count still says zero rows."""
+    if sel is not None and sel.numel() == 0:
+        sel = torch.zeros(1, dtype=torch.int32, device=sel.device)
+        _keep_alive.append(sel)
+        del _keep_alive[:-8]
+    return _ptr(sel)
+
+
+_keep_alive: list = []
+
+
+def _stream(stream) -> ctypes.c_void_p:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _col(t: torch.Tensor) -> px_col:
+    if t.dtype not in _TYPES:
+        raise TypeError(f"unsupported column dtype {t.dtype}")
+    if not t.is_cuda or not t.is_contiguous() or t.dim() != 1:
+        raise ValueError("columns must be contiguous 1-D CUDA tensors")
+    return px_col(_TYPES[t.dtype], 0, t.data_ptr())
+
+
+class _Batch:
+    """A px_batch plus the ctypes storage it points into."""
+
+    def __init__(self, cols, nrows=None, d_nrows=None):
+        self.cols = list(cols)
+        self.arr = (px_col * max(1, len(self.cols)))(*[_col(c) for c in self.cols])
+        n = nrows if nrows is not None else (self.cols[0].numel() if self.cols else 0)
+        self.b = px_batch(len(self.cols), 0, ctypes.cast(self.arr, ctypes.POINTER(px_col)), n, _ptr(d_nrows))
+
+    def ref(self):
+        return ctypes.byref(self.b)
+
+
+class Workspace:
+    """Caller-owned device workspace (a torch uint8 tensor), grown on demand.
+
+    The first 256 bytes hold the sticky status word; px_ws_init clears them."""
+
+    def __init__(self, nbytes: int = 1 << 20, device=None, stream=None):
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self.buf = torch.zeros(max(nbytes, 256), dtype=torch.uint8, device=self.device)
+
+    def ensure(self, nbytes: int, stream=None):
+        if self.buf.numel() < nbytes:
+            self.buf = torch.zeros(int(nbytes * 1.25) + 256, dtype=torch.uint8, device=self.device)
+        return self
+
+    @property
+    def ptr(self) -> int:
+        return self.buf.data_ptr()
+
+    @property
+    def nbytes(self) -> int:
+        return self.buf.numel()
+
+    def reset(self, stream=None):
+        _check(load().px_ws_init(self.ptr, self.nbytes, _stream(stream)), "px_ws_init")
+
+    def status(self, stream=None) -> int:
+        return int(load().px_stream_status(_stream(stream), self.ptr))
+
+
+def _ws(ws, need, stream):
+    if ws is None:
+        ws = Workspace(need)
+    ws.ensure(need, stream)
+    return ws
+
+
+def px_stream_status(ws: Workspace, stream=None) -> int:
+    """Synchronise the stream and return the workspace's sticky status word."""
+    return ws.status(stream)
+
+
+def px_ws_init(ws: Workspace, stream=None):
+    ws.reset(stream)
+
+
+def px_filter(col, lo: int, hi: int, *, d_nrows=None, sel=None, nsel=None, ws=None, stream=None):
+    """Selection of rows with lo <= col < hi (FilterProject, Sec. 3.2). Returns (sel, nsel)."""
+    L = load()
+    n = col.numel()
+    sel = sel if sel is not None else torch.empty(max(n, 1), dtype=torch.int32, device=col.device)
+    nsel = nsel if nsel is not None else torch.empty(1, dtype=torch.int64, device=col.device)
+    ws = _ws(ws, L.px_filter_ws_bytes(n), stream)
+    c = _col(col)
+    _check(L.px_filter(ctypes.byref(c), n, _ptr(d_nrows), int(lo), int(hi), _ptr(sel), _ptr(nsel),
+                       ws.ptr, ws.nbytes, _stream(stream)), "px_filter")
+    return sel, nsel
+
+
+def px_partition(cols, key_col: int, nparts: int, seed: int = 0, *, sel=None, nsel=None, d_nrows=None,
+                 out=None, offsets=None, ws=None, stream=None):
+    """Hash repartition into nparts stable segments (the exchange, Sec. 3.1/3.3.2).
+
+    Returns (out_cols, offsets int64[nparts+1])."""
+    L = load()
+    n = cols[0].numel()
+    inb = _Batch(cols, n, d_nrows)
+    out = out if out is not None else [torch.empty(max(n, 1), dtype=c.dtype, device=c.device) for c in cols]
+    outb = _Batch(out, max(n, 1))
+    offsets = offsets if offsets is not None else torch.empty(nparts + 1, dtype=torch.int64, device=cols[0].device)
+    ws = _ws(ws, L.px_partition_ws_bytes(n, nparts), stream)
+    _check(L.px_partition(inb.ref(), key_col, _sel_ptr(sel), _ptr(nsel), nparts, int(seed) & (2**64 - 1), outb.ref(),
+                          _ptr(offsets), ws.ptr, ws.nbytes, _stream(stream)), "px_partition")
+    return out, offsets
+
+
+def px_join_build(cols, pk_col: int, *, seg=None, unique: bool = True, d_nrows=None, table=None, ws=None,
+                  stream=None):
+    """Build a (per-segment) hash table on cols[pk_col] (join build pipeline). Returns the table tensor."""
+    L = load()
+    n = cols[0].numel()
+    nsegs = 0 if seg is None else seg.numel() - 1
+    need = L.px_join_table_bytes(n, nsegs)
+    table = table if table is not None and table.numel() >= need else torch.empty(
+        need, dtype=torch.uint8, device=cols[0].device)
+    b = _Batch(cols, n, d_nrows)
+    ws = _ws(ws, L.px_join_build_ws_bytes(n), stream)
+    _check(L.px_join_build(b.ref(), pk_col, _ptr(seg), nsegs, 1 if unique else 0, table.data_ptr(), table.numel(),
+                           ws.ptr, ws.nbytes, _stream(stream)), "px_join_build")
+    return table
+
+
+def px_join_probe(table, cols, fk_col: int, *, sel=None, nsel=None, seg=None, d_nrows=None, carry=(),
+                  payload=None, out_cap=None, out=None, probe_row=False, build_row=False, out_seg=False,
+                  ws=None, stream=None):
+    """Inner equi-join probe (join probe pipeline). Returns a dict with 'cols' (carried probe
+    columns then payload columns), 'nout' (device int64[1]) and optionally 'probe_row',
+    'build_row' (int32) and 'out_seg' (int64[nsegs+1])."""
+    L = load()
+    n = cols[0].numel()
+    dev = cols[0].device
+    nsegs = 0 if seg is None else seg.numel() - 1
+    cap = out_cap if out_cap is not None else max(n, 1)
+    carry = list(carry)
+    pay = list(payload) if payload is not None else []
+    if out is None:
+        out = [torch.empty(cap, dtype=cols[c].dtype, device=dev) for c in carry] + \
+              [torch.empty(cap, dtype=p.dtype, device=dev) for p in pay]
+    pb = _Batch(cols, n, d_nrows)
+    payb = _Batch(pay) if pay else None
+    outb = _Batch(out, cap)
+    res = {"cols": out, "nout": torch.empty(1, dtype=torch.int64, device=dev)}
+    if probe_row:
+        res["probe_row"] = torch.empty(cap, dtype=torch.int32, device=dev)
+    if build_row:
+        res["build_row"] = torch.empty(cap, dtype=torch.int32, device=dev)
+    if out_seg:
+        res["out_seg"] = torch.empty(max(nsegs, 1) + 1, dtype=torch.int64, device=dev)
+    carr = (ctypes.c_int32 * max(1, len(carry)))(*carry)
+    ws = _ws(ws, L.px_join_probe_ws_bytes(n), stream)
+    _check(L.px_join_probe(table.data_ptr(), pb.ref(), fk_col, _sel_ptr(sel), _ptr(nsel), _ptr(seg), nsegs,
+                           carr, len(carry), payb.ref() if payb else None, outb.ref(),
+                           _ptr(res.get("probe_row")), _ptr(res.get("build_row")), _ptr(res["nout"]),
+                           _ptr(res.get("out_seg")), ws.ptr, ws.nbytes, _stream(stream)), "px_join_probe")
+    return res
+
+
+def px_groupby_agg(cols, key_cols, aggs, *, max_groups: int, sel=None, nsel=None, seg=None, d_nrows=None,
+                   out=None, ws=None, stream=None):
+    """GROUP BY key_cols computing aggs = [(op, a, b), ...] (HashAggregation, Sec. 3.2).
+
+    Returns a dict with 'keys' (list of key columns), 'aggs' (list of int64 columns),
+    'seg' (int32 segment per group when segmented) and 'ngroups' (device int64[1]); the
+    first ngroups rows are valid, in unspecified order."""
+    L = load()
+    n = cols[0].numel()
+    dev = cols[0].device
+    nsegs = 0 if seg is None else seg.numel() - 1
+    if out is None:
+        out = [torch.empty(max_groups, dtype=cols[k].dtype, device=dev) for k in key_cols] + \
+              [torch.empty(max_groups, dtype=torch.int64, device=dev) for _ in aggs]
+    inb = _Batch(cols, n, d_nrows)
+    outb = _Batch(out, max_groups)
+    karr = (ctypes.c_int32 * len(key_cols))(*key_cols)
+    aarr = (px_agg * max(1, len(aggs)))(*[px_agg(op, a if a is not None else -1, b if b is not None else -1)
+                                          for op, a, b in aggs])
+    res = {"keys": out[:len(key_cols)], "aggs": out[len(key_cols):],
+           "ngroups": torch.empty(1, dtype=torch.int64, device=dev)}
+    if nsegs > 0:
+        res["seg"] = torch.empty(max_groups, dtype=torch.int32, device=dev)
+    ws = _ws(ws, L.px_groupby_ws_bytes(n, max_groups), stream)
+    _check(L.px_groupby_agg(inb.ref(), karr, len(key_cols), aarr, len(aggs), _sel_ptr(sel), _ptr(nsel), _ptr(seg),
+                            nsegs, max_groups, outb.ref(), _ptr(res.get("seg")), _ptr(res["ngroups"]), ws.ptr,
+                            ws.nbytes, _stream(stream)), "px_groupby_agg")
+    return res

@@ -1,0 +1,134 @@
+"""The three operator pipelines of the workloads, each a chain of px_* calls on one
+stream with every buffer allocated once up front (so a step allocates nothing and
+never synchronises with the host).
+
+* PlainPipeline      - filter -> hash exchange -> group-by (a Q1-like scan-filter-
+                       aggregate, Sec. 2.3), over one columnar batch.
+* JoinPipeline       - filter -> join build -> join probe -> group-by (a Q5/Q9-like
+                       filter-join-aggregate, Sec. 3.4).
+* AtScalePipeline    - exchange of both join sides into P partitions -> per-partition
+                       join build and probe -> Partial group-by per partition -> Final
+                       merge (the exchange feeding the join and aggregation, Sec. 3.3
+                       with the aggregation modes of Sec. 3.2).
+"""
+from __future__ import annotations
+
+import torch
+
+from . import (PX_COUNT, PX_SUM, PX_SUM_MUL, Workspace, load, px_filter, px_groupby_agg, px_join_build,
+               px_join_probe, px_partition)
+
+
+def _empty_like_cols(cols, n=None):
+    return [torch.empty(max(n if n is not None else c.numel(), 1), dtype=c.dtype, device=c.device) for c in cols]
+
+
+class PlainPipeline:
+    """date filter -> partition on key -> group by (flag, status): SUM(price),
+    SUM(price*qty), SUM(qty), COUNT(*)."""
+
+    NAMES = ["key", "price", "qty", "date", "flag", "status"]
+
+    def __init__(self, d: dict, lo: int, hi: int, nparts: int = 8, seed: int = 0, max_groups: int = 256):
+        L = load()
+        self.d = d
+        self.lo, self.hi, self.nparts, self.seed, self.max_groups = lo, hi, nparts, seed, max_groups
+        n = d["key"].numel()
+        dev = d["key"].device
+        self.cols = [d[k] for k in self.NAMES]
+        self.sel = torch.empty(max(n, 1), dtype=torch.int32, device=dev)
+        self.nsel = torch.empty(1, dtype=torch.int64, device=dev)
+        self.parts = _empty_like_cols(self.cols)
+        self.offsets = torch.empty(nparts + 1, dtype=torch.int64, device=dev)
+        self.gout = [torch.empty(max_groups, dtype=torch.int8, device=dev) for _ in range(2)] + \
+                    [torch.empty(max_groups, dtype=torch.int64, device=dev) for _ in range(4)]
+        need = max(L.px_filter_ws_bytes(n), L.px_partition_ws_bytes(n, nparts), L.px_groupby_ws_bytes(n, max_groups))
+        self.ws = Workspace(need)
+
+    def run(self, stream=None) -> dict:
+        px_filter(self.d["date"], self.lo, self.hi, sel=self.sel, nsel=self.nsel, ws=self.ws, stream=stream)
+        px_partition(self.cols, 0, self.nparts, self.seed, sel=self.sel, nsel=self.nsel, out=self.parts,
+                     offsets=self.offsets, ws=self.ws, stream=stream)
+        g = px_groupby_agg(self.parts, [4, 5], [(PX_SUM, 1, None), (PX_SUM_MUL, 1, 2), (PX_SUM, 2, None),
+                                                (PX_COUNT, None, None)],
+                           max_groups=self.max_groups, d_nrows=self.nsel, out=self.gout, ws=self.ws, stream=stream)
+        return {"sel": self.sel, "nsel": self.nsel, "parts": dict(zip(self.NAMES, self.parts)),
+                "offsets": self.offsets, "groups": g}
+
+
+class JoinPipeline:
+    """fact.date filter -> build on dim.pk -> probe fact.fk (carry amount, gather
+    dim.attr) -> group by attr: SUM(amount), COUNT(*)."""
+
+    def __init__(self, d: dict, lo: int, hi: int, max_groups: int = 64):
+        L = load()
+        self.d = d
+        self.lo, self.hi, self.max_groups = lo, hi, max_groups
+        nf, nd = d["fk"].numel(), d["pk"].numel()
+        dev = d["fk"].device
+        self.fact = [d["fk"], d["amount"], d["date"]]
+        self.dim = [d["pk"], d["attr"]]
+        self.sel = torch.empty(max(nf, 1), dtype=torch.int32, device=dev)
+        self.nsel = torch.empty(1, dtype=torch.int64, device=dev)
+        self.table = torch.empty(L.px_join_table_bytes(nd, 0), dtype=torch.uint8, device=dev)
+        self.jout = [torch.empty(max(nf, 1), dtype=torch.int64, device=dev),
+                     torch.empty(max(nf, 1), dtype=torch.int32, device=dev)]
+        self.gout = [torch.empty(max_groups, dtype=torch.int32, device=dev)] + \
+                    [torch.empty(max_groups, dtype=torch.int64, device=dev) for _ in range(2)]
+        need = max(L.px_filter_ws_bytes(nf), L.px_join_build_ws_bytes(nd), L.px_join_probe_ws_bytes(nf),
+                   L.px_groupby_ws_bytes(nf, max_groups))
+        self.ws = Workspace(need)
+
+    def run(self, stream=None) -> dict:
+        px_filter(self.d["date"], self.lo, self.hi, sel=self.sel, nsel=self.nsel, ws=self.ws, stream=stream)
+        px_join_build(self.dim, 0, unique=True, table=self.table, ws=self.ws, stream=stream)
+        j = px_join_probe(self.table, self.fact, 0, sel=self.sel, nsel=self.nsel, carry=[1], payload=[self.d["attr"]],
+                          out=self.jout, out_cap=self.jout[0].numel(), ws=self.ws, stream=stream)
+        g = px_groupby_agg(self.jout, [1], [(PX_SUM, 0, None), (PX_COUNT, None, None)], max_groups=self.max_groups,
+                           d_nrows=j["nout"], out=self.gout, ws=self.ws, stream=stream)
+        return {"sel": self.sel, "nsel": self.nsel, "join": j, "groups": g}
+
+
+class AtScalePipeline:
+    """Exchange both sides on the join key into nparts partitions, join per partition,
+    Partial group-by attr per partition (SUM(amount), COUNT(*)), Final merge by attr."""
+
+    def __init__(self, d: dict, nparts: int = 64, seed: int = 0, nattr_bound: int = 10_000):
+        L = load()
+        self.d = d
+        self.nparts, self.seed = nparts, seed
+        nf, nd = d["fk"].numel(), d["pk"].numel()
+        dev = d["fk"].device
+        self.fact = [d["fk"], d["amount"], d["date"]]
+        self.dim = [d["pk"], d["attr"]]
+        self.fparts = _empty_like_cols(self.fact)
+        self.dparts = _empty_like_cols(self.dim)
+        self.foff = torch.empty(nparts + 1, dtype=torch.int64, device=dev)
+        self.doff = torch.empty(nparts + 1, dtype=torch.int64, device=dev)
+        self.table = torch.empty(L.px_join_table_bytes(nd, nparts), dtype=torch.uint8, device=dev)
+        self.jout = [torch.empty(max(nf, 1), dtype=torch.int64, device=dev),
+                     torch.empty(max(nf, 1), dtype=torch.int32, device=dev)]
+        self.max_partial = min(max(nf, 1), nparts * nattr_bound)
+        self.max_final = min(max(nf, 1), nattr_bound)
+        self.pout = [torch.empty(self.max_partial, dtype=torch.int32, device=dev)] + \
+                    [torch.empty(self.max_partial, dtype=torch.int64, device=dev) for _ in range(2)]
+        self.fout = [torch.empty(self.max_final, dtype=torch.int32, device=dev)] + \
+                    [torch.empty(self.max_final, dtype=torch.int64, device=dev) for _ in range(2)]
+        need = max(L.px_partition_ws_bytes(nf, nparts), L.px_partition_ws_bytes(nd, nparts),
+                   L.px_join_build_ws_bytes(nd), L.px_join_probe_ws_bytes(nf),
+                   L.px_groupby_ws_bytes(nf, self.max_partial))
+        self.ws = Workspace(need)
+
+    def run(self, stream=None) -> dict:
+        P, ws = self.nparts, self.ws
+        px_partition(self.dim, 0, P, self.seed, out=self.dparts, offsets=self.doff, ws=ws, stream=stream)
+        px_partition(self.fact, 0, P, self.seed, out=self.fparts, offsets=self.foff, ws=ws, stream=stream)
+        px_join_build(self.dparts, 0, seg=self.doff, unique=True, table=self.table, ws=ws, stream=stream)
+        j = px_join_probe(self.table, self.fparts, 0, seg=self.foff, carry=[1], payload=[self.dparts[1]],
+                          out=self.jout, out_cap=self.jout[0].numel(), out_seg=True, ws=ws, stream=stream)
+        part = px_groupby_agg(self.jout, [1], [(PX_SUM, 0, None), (PX_COUNT, None, None)],
+                              max_groups=self.max_partial, seg=j["out_seg"], d_nrows=j["nout"], out=self.pout,
+                              ws=ws, stream=stream)
+        final = px_groupby_agg(self.pout, [0], [(PX_SUM, 1, None), (PX_SUM, 2, None)], max_groups=self.max_final,
+                               d_nrows=part["ngroups"], out=self.fout, ws=ws, stream=stream)
+        return {"dim_offsets": self.doff, "fact_offsets": self.foff, "join": j, "partial": part, "final": final}

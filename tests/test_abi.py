@@ -1,0 +1,128 @@
+"""The C ABI without a GPU: libpx.so builds, loads, exports every function that
+include/px.h declares, and rejects bad arguments on the host (before any CUDA
+call) with the documented status codes and a message."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADERS = [os.path.join(ROOT, "include", f) for f in sorted(os.listdir(os.path.join(ROOT, "include")))
+           if f.endswith(".h")]
+
+
+def declared_functions():
+    names = []
+    for h in HEADERS:
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        names += re.findall(r"^\s*(?:px_status|size_t|uint64_t|const char\*)\s+(px_\w+)\s*\(", text, flags=re.M)
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2606_24647_gb300 import build
+    path = build.build()
+    import paper_2606_24647_gb300 as pxm
+    return pxm.load(path)
+
+
+def test_header_declares_the_five_operators():
+    names = set(declared_functions())
+    for op in ["px_filter", "px_partition", "px_join_build", "px_join_probe", "px_groupby_agg"]:
+        assert op in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    from paper_2606_24647_gb300 import LIB_PATH
+    out = subprocess.run(["nm", "-D", "--defined-only", LIB_PATH], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\bT (px_\w+)$", out, flags=re.M))
+    missing = [n for n in declared_functions() if n not in exported]
+    assert not missing, missing
+    for n in declared_functions():
+        assert hasattr(lib, n)
+
+
+def test_binding_declares_every_symbol():
+    import paper_2606_24647_gb300 as pxm
+    assert sorted(pxm.EXPORTED) == sorted(declared_functions())
+
+
+FAKE = 0x7f0000000000  # 16-byte aligned, never dereferenced: every case fails a host check first
+
+
+def _batch(pxm, types, nrows, ptrs=None):
+    cols = (pxm.px_col * len(types))(*[pxm.px_col(t, 0, (ptrs or [FAKE + 4096 * i for i in range(len(types))])[i])
+                                       for i, t in enumerate(types)])
+    b = pxm.px_batch(len(types), 0, ctypes.cast(cols, ctypes.POINTER(pxm.px_col)), nrows, None)
+    b._keep = cols
+    return b
+
+
+def test_workspace_sizes_are_monotone(lib):
+    for f, args in [(lib.px_filter_ws_bytes, [(10,), (10_000,), (10_000_000,)]),
+                    (lib.px_partition_ws_bytes, [(10, 8), (10_000, 8), (10_000, 64), (10_000_000, 64)]),
+                    (lib.px_join_probe_ws_bytes, [(10,), (10_000,), (10_000_000,)]),
+                    (lib.px_groupby_ws_bytes, [(10, 1), (10, 1000), (10, 100_000)])]:
+        sizes = [f(*a) for a in args]
+        assert sizes == sorted(sizes) and sizes[0] >= 256
+    assert lib.px_join_table_bytes(1000, 0) < lib.px_join_table_bytes(2000, 0)
+    assert lib.px_join_table_bytes(1000, 64) >= 16 * 2 * 1000
+
+
+def test_host_checks(lib):
+    import paper_2606_24647_gb300 as pxm
+    ws = FAKE
+    wsz = 1 << 30
+    # filter: null column, unknown type, misaligned data, null outputs
+    assert lib.px_filter(None, 10, None, 0, 1, FAKE, FAKE, ws, wsz, None) == pxm.PX_ERR_INVALID
+    bad = pxm.px_col(3, 0, FAKE)
+    assert lib.px_filter(ctypes.byref(bad), 10, None, 0, 1, FAKE, FAKE, ws, wsz, None) == pxm.PX_ERR_INVALID
+    assert "type" in pxm.last_error()
+    mis = pxm.px_col(pxm.PX_I32, 0, FAKE + 4)
+    assert lib.px_filter(ctypes.byref(mis), 10, None, 0, 1, FAKE, FAKE, ws, wsz, None) == pxm.PX_ERR_INVALID
+    assert "aligned" in pxm.last_error()
+    ok = pxm.px_col(pxm.PX_I32, 0, FAKE)
+    assert lib.px_filter(ctypes.byref(ok), 10, None, 0, 1, None, FAKE, ws, wsz, None) == pxm.PX_ERR_INVALID
+    assert lib.px_filter(ctypes.byref(ok), 10, None, 0, 1, FAKE, FAKE, ws, 16, None) == pxm.PX_ERR_INVALID
+    assert "workspace" in pxm.last_error()
+    # partition: non-int64 key, bad nparts, column count / type mismatch
+    inb = _batch(pxm, [pxm.PX_I64, pxm.PX_I32], 100)
+    outb = _batch(pxm, [pxm.PX_I64, pxm.PX_I32], 100)
+    r = lib.px_partition(ctypes.byref(inb), 1, None, None, 8, 0, ctypes.byref(outb), FAKE, ws, wsz, None)
+    assert r == pxm.PX_ERR_INVALID
+    for P in [0, pxm_max_parts() + 1]:
+        r = lib.px_partition(ctypes.byref(inb), 0, None, None, P, 0, ctypes.byref(outb), FAKE, ws, wsz, None)
+        assert r == pxm.PX_ERR_UNSUPPORTED
+    out_bad = _batch(pxm, [pxm.PX_I64, pxm.PX_I64], 100)
+    r = lib.px_partition(ctypes.byref(inb), 0, None, None, 8, 0, ctypes.byref(out_bad), FAKE, ws, wsz, None)
+    assert r == pxm.PX_ERR_INVALID
+    small = _batch(pxm, [pxm.PX_I64, pxm.PX_I32], 50)
+    r = lib.px_partition(ctypes.byref(inb), 0, None, None, 8, 0, ctypes.byref(small), FAKE, ws, wsz, None)
+    assert r == pxm.PX_ERR_INVALID and "capacity" in pxm.last_error()
+    # selection pointer without its count
+    r = lib.px_partition(ctypes.byref(inb), 0, FAKE, None, 8, 0, ctypes.byref(outb), FAKE, ws, wsz, None)
+    assert r == pxm.PX_ERR_INVALID
+    # join build: table too small, segments without offsets
+    b = _batch(pxm, [pxm.PX_I64], 100)
+    assert lib.px_join_build(ctypes.byref(b), 0, None, 0, 1, FAKE, 64, ws, wsz, None) == pxm.PX_ERR_INVALID
+    assert lib.px_join_build(ctypes.byref(b), 0, None, 4, 1, FAKE, 1 << 30, ws, wsz, None) == pxm.PX_ERR_INVALID
+    # group-by: too many key bits with segments, wrong output arity
+    g_in = _batch(pxm, [pxm.PX_I64, pxm.PX_I64], 100)
+    g_out = _batch(pxm, [pxm.PX_I64, pxm.PX_I64], 100)
+    keys = (ctypes.c_int32 * 1)(0)
+    aggs = (pxm.px_agg * 1)(pxm.px_agg(pxm.PX_SUM, 1, -1))
+    r = lib.px_groupby_agg(ctypes.byref(g_in), keys, 1, aggs, 1, None, None, FAKE, 4, 100, ctypes.byref(g_out),
+                           None, FAKE, ws, wsz, None)
+    assert r == pxm.PX_ERR_UNSUPPORTED and "bits" in pxm.last_error()
+    r = lib.px_groupby_agg(ctypes.byref(g_in), keys, 1, aggs, 1, None, None, None, 0, 100, ctypes.byref(inb),
+                           None, FAKE, ws, wsz, None)
+    assert r == pxm.PX_ERR_INVALID
+
+
+def pxm_max_parts():
+    text = open(os.path.join(ROOT, "include", "px.h")).read()
+    return int(re.search(r"#define PX_MAX_PARTS (\d+)", text).group(1))

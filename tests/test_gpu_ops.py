@@ -1,0 +1,289 @@
+"""GPU parity of each operator against the CPU oracle, element by element, on
+seeded inputs that span many tiles, ragged tails and the edge cases (empty
+inputs, one row, all rows in one partition, duplicate keys, wrap-around sums,
+capacity overflow). All integer work: the bar is bit-exact."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import pxdata
+from gpu_helpers import assert_groups_equal, count, dev, host
+
+pytestmark = pytest.mark.gpu
+
+SIZES = [0, 1, 31, 2047, 2048, 2049, 4095, 4096, 4097, 100_003]
+
+
+# -------------------------------------------------------------- filter -----
+
+@pytest.mark.parametrize("dtype", [np.int8, np.int32, np.int64])
+def test_filter_parity(px, dtype):
+    g = pxdata.rng(100)
+    info = np.iinfo(dtype)
+    for n in SIZES:
+        col = pxdata.random_column(g, n, dtype)
+        for lo, hi in [(info.min, info.max), (-10, 10**6), (0, 0), (int(info.max), int(info.min)),
+                       (-(2**63), 2**63 - 1)]:
+            sel, nsel = px.px_filter(dev(col), lo, hi)
+            want = oracle.filter(col, lo, hi)
+            assert count(nsel) == want.size
+            np.testing.assert_array_equal(host(sel, want.size), want)
+
+
+def test_filter_device_row_count(px):
+    g = pxdata.rng(101)
+    col = pxdata.random_column(g, 50_000, np.int32, 0, 2556)
+    for n in [0, 1, 12_345, 50_000]:
+        d_n = dev(np.array([n], np.int64))
+        sel, nsel = px.px_filter(dev(col), 100, 2000, d_nrows=d_n)
+        want = oracle.filter(col[:n], 100, 2000)
+        assert count(nsel) == want.size
+        np.testing.assert_array_equal(host(sel, want.size), want)
+
+
+# ----------------------------------------------------------- partition -----
+
+def _part_cols(g, n):
+    return [pxdata.random_column(g, n, np.int64, -(2**40), 2**40),
+            pxdata.random_column(g, n, np.int32),
+            pxdata.random_column(g, n, np.int8),
+            np.arange(n, dtype=np.int64)]
+
+
+@pytest.mark.parametrize("P", [1, 2, 3, 8, 64, 1000, 1024])
+def test_partition_parity(px, P):
+    g = pxdata.rng(200 + P)
+    for n in [0, 1, 4095, 4096, 4097, 60_001]:
+        cols = _part_cols(g, n)
+        for seed in [0, 0xDEADBEEF12345678]:
+            out, off = px.px_partition([dev(c) for c in cols], 0, P, seed)
+            want, woff = oracle.partition(cols, 0, P, seed)
+            np.testing.assert_array_equal(host(off), woff)
+            for a, b in zip(out, want):
+                np.testing.assert_array_equal(host(a, n), b)
+
+
+def test_partition_with_selection_and_key_not_first(px):
+    g = pxdata.rng(210)
+    n = 70_001
+    cols = _part_cols(g, n)
+    cols = [cols[1], cols[0], cols[2], cols[3]]
+    sel = oracle.filter(cols[1], -(2**39), 2**39)
+    out, off = px.px_partition([dev(c) for c in cols], 1, 64, 7, sel=dev(sel), nsel=dev(np.array([sel.size])))
+    want, woff = oracle.partition(cols, 1, 64, 7, sel=sel)
+    np.testing.assert_array_equal(host(off), woff)
+    for a, b in zip(out, want):
+        np.testing.assert_array_equal(host(a, sel.size), b)
+
+
+def test_partition_skew_all_one_key(px):
+    n = 50_000
+    key = np.full(n, 42, np.int64)
+    rid = np.arange(n, dtype=np.int32)
+    out, off = px.px_partition([dev(key), dev(rid)], 0, 64, 0)
+    want, woff = oracle.partition([key, rid], 0, 64, 0)
+    np.testing.assert_array_equal(host(off), woff)
+    np.testing.assert_array_equal(host(out[1], n), want[1])
+
+
+def test_partition_device_row_count(px):
+    g = pxdata.rng(211)
+    cols = _part_cols(g, 30_000)
+    for n in [0, 5, 9_999]:
+        out, off = px.px_partition([dev(c) for c in cols], 0, 8, 0, d_nrows=dev(np.array([n], np.int64)))
+        want, woff = oracle.partition([c[:n] for c in cols], 0, 8, 0)
+        np.testing.assert_array_equal(host(off), woff)
+        for a, b in zip(out, want):
+            np.testing.assert_array_equal(host(a, n), b)
+
+
+# ---------------------------------------------------------------- join -----
+
+def _join(px, pk, fk, unique=True, sel=None, bseg=None, pseg=None, out_cap=None, payload_dtype=np.int32):
+    g = pxdata.rng(300)
+    attr = pxdata.random_column(g, pk.size, payload_dtype)
+    amount = pxdata.random_column(g, fk.size, np.int64)
+    ws = px.Workspace(1 << 20)
+    table = px.px_join_build([dev(pk)], 0, seg=None if bseg is None else dev(bseg), unique=unique, ws=ws)
+    kw = {}
+    if sel is not None:
+        kw = {"sel": dev(sel), "nsel": dev(np.array([sel.size], np.int64))}
+    res = px.px_join_probe(table, [dev(fk), dev(amount)], 0, carry=[1], payload=[dev(attr)],
+                           seg=None if pseg is None else dev(pseg), probe_row=True, build_row=True,
+                           out_seg=pseg is not None, out_cap=out_cap, ws=ws, **kw)
+    return res, attr, amount, ws
+
+
+def test_join_unique_parity(px):
+    g = pxdata.rng(301)
+    for nb, nprobe in [(0, 100), (100, 0), (1, 1), (1000, 5000), (20_000, 100_003)]:
+        pk = (g.permutation(3 * max(nb, 1))[:nb] - nb).astype(np.int64)
+        fk = pxdata.random_column(g, nprobe, np.int64, -nb, 2 * nb)
+        for sel in [None, oracle.filter(pxdata.random_column(g, nprobe, np.int32, 0, 9), 0, 3)]:
+            res, attr, amount, ws = _join(px, pk, fk, sel=sel)
+            assert ws.status() == px.PX_OK
+            pr, br, _ = oracle.join(pk, fk, sel=sel)
+            m = count(res["nout"])
+            assert m == pr.size
+            np.testing.assert_array_equal(host(res["probe_row"], m), pr)
+            np.testing.assert_array_equal(host(res["build_row"], m), br)
+            np.testing.assert_array_equal(host(res["cols"][0], m), amount[pr])
+            np.testing.assert_array_equal(host(res["cols"][1], m), attr[br])
+
+
+def test_join_multi_match_parity(px):
+    g = pxdata.rng(302)
+    pk = pxdata.random_column(g, 3000, np.int64, 0, 700)       # ~4 duplicates per key
+    fk = pxdata.random_column(g, 20_000, np.int64, -50, 750)
+    pr, br, _ = oracle.join(pk, fk)
+    res, attr, amount, ws = _join(px, pk, fk, unique=False, out_cap=pr.size)
+    assert ws.status() == px.PX_OK
+    m = count(res["nout"])
+    assert m == pr.size
+    gpr, gbr = host(res["probe_row"], m), host(res["build_row"], m)
+    np.testing.assert_array_equal(gpr, pr)            # probe order is unique
+    # the matches of one probe row may come in any order: compare per-row multisets
+    order_g = np.lexsort((gbr, gpr))
+    np.testing.assert_array_equal(gbr[order_g], br)
+    np.testing.assert_array_equal(host(res["cols"][0], m), amount[gpr])
+    np.testing.assert_array_equal(host(res["cols"][1], m), attr[gbr])
+
+
+def test_join_segmented_parity(px):
+    g = pxdata.rng(303)
+    d = pxdata.plain_at_scale(20_000, 300_000, nattr=50)
+    dparts, doff = oracle.partition([d["pk"]], 0, 64, 0)
+    fparts, foff = oracle.partition([d["fk"]], 0, 64, 0)
+    res, attr, amount, ws = _join(px, dparts[0], fparts[0], bseg=doff, pseg=foff)
+    assert ws.status() == px.PX_OK
+    pr, br, oseg = oracle.join(dparts[0], fparts[0], build_seg=doff, probe_seg=foff)
+    m = count(res["nout"])
+    assert m == pr.size == 300_000
+    np.testing.assert_array_equal(host(res["probe_row"], m), pr)
+    np.testing.assert_array_equal(host(res["build_row"], m), br)
+    np.testing.assert_array_equal(host(res["out_seg"]), oseg)
+
+
+def test_join_segments_with_empty_segments(px):
+    g = pxdata.rng(304)
+    pk = pxdata.random_column(g, 500, np.int64, 0, 300)
+    pk = np.unique(pk)
+    fk = pxdata.random_column(g, 4000, np.int64, 0, 300)
+    bseg = np.array([0, 0, pk.size // 3, pk.size // 3, pk.size, pk.size], np.int64)
+    pseg = np.array([0, 100, 100, 2500, 4000, 4000], np.int64)
+    res, attr, amount, ws = _join(px, pk, fk, bseg=bseg, pseg=pseg)
+    assert ws.status() == px.PX_OK
+    pr, br, oseg = oracle.join(pk, fk, build_seg=bseg, probe_seg=pseg)
+    m = count(res["nout"])
+    assert m == pr.size
+    np.testing.assert_array_equal(host(res["probe_row"], m), pr)
+    np.testing.assert_array_equal(host(res["build_row"], m), br)
+    np.testing.assert_array_equal(host(res["out_seg"]), oseg)
+
+
+def test_join_duplicate_key_is_reported(px):
+    pk = np.array([5, 6, 7, 6], np.int64)
+    ws = px.Workspace(1 << 16)
+    px.px_join_build([dev(pk)], 0, unique=True, ws=ws)
+    assert ws.status() == px.PX_ERR_DUPLICATE_KEY
+
+
+def test_join_reserved_key_is_reported(px):
+    pk = np.array([5, -(2**63), 7], np.int64)
+    ws = px.Workspace(1 << 16)
+    px.px_join_build([dev(pk)], 0, unique=True, ws=ws)
+    assert ws.status() == px.PX_ERR_UNSUPPORTED
+
+
+def test_join_capacity_overflow_reports_required_size(px):
+    pk = np.arange(100, dtype=np.int64)
+    fk = np.tile(np.arange(100, dtype=np.int64), 30)
+    res, attr, amount, ws = _join(px, pk, fk, out_cap=1000)
+    assert ws.status() == px.PX_ERR_CAPACITY
+    assert count(res["nout"]) == 3000
+    pr, br, _ = oracle.join(pk, fk)
+    np.testing.assert_array_equal(host(res["probe_row"], 1000), pr[:1000])
+
+
+# ------------------------------------------------------------ group-by -----
+
+def _gb(px, cols, key_idx, aggs, max_groups, **kw):
+    return px.px_groupby_agg([dev(c) for c in cols], key_idx, aggs, max_groups=max_groups, **kw)
+
+
+@pytest.mark.parametrize("kt", [(np.int8,), (np.int32,), (np.int64,), (np.int8, np.int8), (np.int32, np.int8),
+                                (np.int32, np.int32)])
+def test_groupby_parity(px, kt):
+    g = pxdata.rng(400)
+    for n in [0, 1, 2047, 2049, 100_003]:
+        for dom in [3, 300, 30_000]:
+            keys = [pxdata.random_column(g, n, t, max(np.iinfo(t).min, -dom), min(np.iinfo(t).max, dom))
+                    for t in kt]
+            a64 = pxdata.random_column(g, n, np.int64)
+            a32 = pxdata.random_column(g, n, np.int32)
+            b8 = pxdata.random_column(g, n, np.int8)
+            cols = keys + [a64, a32, b8]
+            nk = len(kt)
+            aggs = [(px.PX_SUM, nk, None), (px.PX_COUNT, None, None), (px.PX_SUM_MUL, nk + 1, nk + 2),
+                    (px.PX_SUM_MUL, nk, nk)]
+            want = oracle.groupby(keys, [(oracle.SUM, a64, None), (oracle.COUNT, None, None),
+                                         (oracle.SUM_MUL, a32, b8), (oracle.SUM_MUL, a64, a64)])
+            res = _gb(px, cols, list(range(nk)), aggs, max(1, want["ngroups"]))
+            assert_groups_equal(res, want, nk)
+
+
+def test_groupby_selection_and_device_count(px):
+    g = pxdata.rng(401)
+    n = 80_000
+    k = pxdata.random_column(g, n, np.int32, 0, 99)
+    a = pxdata.random_column(g, n, np.int64, -10**9, 10**9)
+    sel = oracle.filter(pxdata.random_column(g, n, np.int32, 0, 9), 0, 4)
+    want = oracle.groupby([k], [(oracle.SUM, a, None), (oracle.COUNT, None, None)], sel=sel)
+    res = _gb(px, [k, a], [0], [(px.PX_SUM, 1, None), (px.PX_COUNT, None, None)], 128, sel=dev(sel),
+              nsel=dev(np.array([sel.size], np.int64)))
+    assert_groups_equal(res, want, 1)
+    want = oracle.groupby([k[:5000]], [(oracle.SUM, a[:5000], None), (oracle.COUNT, None, None)])
+    res = _gb(px, [k, a], [0], [(px.PX_SUM, 1, None), (px.PX_COUNT, None, None)], 128,
+              d_nrows=dev(np.array([5000], np.int64)))
+    assert_groups_equal(res, want, 1)
+
+
+def test_groupby_segmented_parity(px):
+    g = pxdata.rng(402)
+    n = 120_000
+    k = pxdata.random_column(g, n, np.int32, 0, 2000)
+    a = pxdata.random_column(g, n, np.int64, 0, 10**6)
+    seg = np.array([0, 0, 100, 101, 60_000, 60_000, 119_999, n], np.int64)
+    want = oracle.groupby([k], [(oracle.SUM, a, None), (oracle.COUNT, None, None)], seg=seg)
+    res = _gb(px, [k, a], [0], [(px.PX_SUM, 1, None), (px.PX_COUNT, None, None)], want["ngroups"], seg=dev(seg))
+    assert_groups_equal(res, want, 1, segmented=True)
+
+
+def test_groupby_hot_key_and_wrap(px):
+    n = 200_000
+    k = np.zeros(n, np.int8)
+    k[::1000] = 1
+    a = np.full(n, 2**62 + 12345, np.int64)   # sums wrap mod 2^64
+    want = oracle.groupby([k], [(oracle.SUM, a, None), (oracle.SUM_MUL, a, a), (oracle.COUNT, None, None)])
+    res = _gb(px, [k, a], [0], [(px.PX_SUM, 1, None), (px.PX_SUM_MUL, 1, 1), (px.PX_COUNT, None, None)], 4)
+    assert_groups_equal(res, want, 1)
+
+
+def test_groupby_many_groups_spill_to_global(px):
+    g = pxdata.rng(403)
+    n = 300_000
+    k = pxdata.random_column(g, n, np.int64, -(2**62), 2**62)   # ~all distinct
+    k[::3] = 77                                                 # plus one hot key
+    a = pxdata.random_column(g, n, np.int64, 0, 1000)
+    want = oracle.groupby([k], [(oracle.SUM, a, None), (oracle.COUNT, None, None)])
+    res = _gb(px, [k, a], [0], [(px.PX_SUM, 1, None), (px.PX_COUNT, None, None)], want["ngroups"])
+    assert_groups_equal(res, want, 1)
+
+
+def test_groupby_capacity_overflow_reported(px):
+    k = np.arange(1000, dtype=np.int32)
+    ws = px.Workspace(1 << 20)
+    res = px.px_groupby_agg([dev(k)], [0], [(px.PX_COUNT, None, None)], max_groups=100, ws=ws)
+    assert ws.status() == px.PX_ERR_CAPACITY
+    assert count(res["ngroups"]) == 1000
