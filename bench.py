@@ -190,7 +190,7 @@ def run_reference(args):
         return 0
     import oracle
     oracle.build()
-    d = pxdata.plain_at_scale(seed=shard_seed(0))
+    d = pxdata.plain_at_scale(NDIM, NFACT, NATTR, seed=shard_seed(0))
     # size each step's sample so the whole run stays within ~2 minutes
     probe_rate, _ = oracle_rate(d, 200_000)
     per_step_s = min(10.0, 120.0 / max(1, args.steps + args.warmup))
@@ -236,7 +236,7 @@ def run_px(args):
     px.load()
     dev = torch.device("cuda", torch.cuda.current_device())
 
-    d = pxdata.plain_at_scale(seed=shard_seed(rank))
+    d = pxdata.plain_at_scale(NDIM, NFACT, NATTR, seed=shard_seed(rank))
     host = {k: torch.from_numpy(v).pin_memory() for k, v in d.items()}
     dd = {k: v.to(dev, non_blocking=True) for k, v in host.items()}
     torch.cuda.synchronize()
@@ -403,12 +403,20 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="px", choices=["px", "reference"])
-    ap.add_argument("--cpu-sample", type=int, default=6_000_000,
+    ap.add_argument("--cpu-sample", type=int, default=30_000_000,
                     help="fact rows of the oracle's CPU-baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--fact-rows", type=int, default=None,
+                    help="smaller fact side for profiling captures (the reported workload is then reduced)")
+    ap.add_argument("--dim-rows", type=int, default=None)
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
+    global NFACT, NDIM, WORKLOAD
+    if args.fact_rows or args.dim_rows:
+        NFACT = args.fact_rows or NFACT
+        NDIM = args.dim_rows or NDIM
+        WORKLOAD = f"REDUCED for profiling: {NFACT}-row fact x {NDIM}-row dim; otherwise " + WORKLOAD
     if args.impl == "reference":
         return run_reference(args)
     return run_px(args)
