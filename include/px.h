@@ -138,6 +138,26 @@ px_status px_filter(const px_col* col, int64_t nrows, const int64_t* d_nrows,
                     int64_t lo, int64_t hi, int32_t* d_sel, int64_t* d_nsel,
                     void* d_ws, size_t ws_bytes, void* stream);
 
+/* Allocation-free px_filter. The paper has no counterpart: this entry point is for
+ * callers that cannot allocate device memory and so cannot pass a workspace - for
+ * instance code embedded in a host engine whose memory manager owns every device
+ * byte, or a serving loop that reserves all memory at start-up and must not call
+ * cudaMalloc (which may synchronise the device) while serving. Same arguments and
+ * results as px_filter, except that its scratch lives in one static device array
+ * of 524,800 bytes inside this library (held by every GPU that loads it until the
+ * process exits), so nrows may not exceed PX_FILTER_NOALLOC_MAX_ROWS
+ * (PX_ERR_UNSUPPORTED otherwise; use px_filter). It allocates nothing. d_status
+ * (nullable, device int32) receives the call's device status word (PX_OK or
+ * PX_ERR_TIMEOUT). The first call on each device looks up the array's device
+ * address on that device (cudaGetSymbolAddress) and caches it; make that first
+ * call before any stream capture. Every call on a device shares the one array and
+ * clears what it uses at its start, so calls whose GPU work may overlap (other
+ * streams, other threads) race and must be serialised by the caller. */
+#define PX_FILTER_NOALLOC_MAX_ROWS 134217728LL /* 65536 tiles of 2048 rows */
+px_status px_filter_noalloc(const px_col* col, int64_t nrows, const int64_t* d_nrows,
+                            int64_t lo, int64_t hi, int32_t* d_sel, int64_t* d_nsel,
+                            int32_t* d_status, void* stream);
+
 /* ---- hash partition: the on-device exchange (Sec. 3.1, Sec. 3.3.2) ------ */
 
 size_t px_partition_ws_bytes(int64_t nrows, int32_t nparts);

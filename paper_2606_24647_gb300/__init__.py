@@ -29,7 +29,7 @@ PX_COUNT, PX_SUM, PX_SUM_MUL = 0, 1, 2
 
 EXPORTED = [
     "px_ws_init", "px_stream_status", "px_last_error", "px_kernel_launches",
-    "px_filter_ws_bytes", "px_filter",
+    "px_filter_ws_bytes", "px_filter", "px_filter_noalloc",
     "px_partition_ws_bytes", "px_partition",
     "px_join_table_bytes", "px_join_build_ws_bytes", "px_join_build",
     "px_join_probe_ws_bytes", "px_join_probe",
@@ -73,6 +73,7 @@ def _declare(lib):
         "px_kernel_launches": ([], U64),
         "px_filter_ws_bytes": ([I64], SZ),
         "px_filter": ([CP, I64, P, I64, I64, P, P, P, SZ, P], I32),
+        "px_filter_noalloc": ([CP, I64, P, I64, I64, P, P, P, P], I32),
         "px_partition_ws_bytes": ([I64, I32], SZ),
         "px_partition": ([BP, I32, P, P, I32, U64, BP, P, P, SZ, P], I32),
         "px_join_table_bytes": ([I64, I32], SZ),

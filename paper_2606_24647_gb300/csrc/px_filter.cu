@@ -4,6 +4,8 @@
 // passing rows with warp ballots, gets the tile's output offset from a bounded
 // decoupled look-back, and writes the passing row indices in ascending order.
 // HBM traffic: the column once plus 4 bytes per passing row.
+#include <mutex>
+
 #include "px_common.cuh"
 
 namespace px {
@@ -118,3 +120,97 @@ px_status px_filter(const px_col* col, int64_t nrows, const int64_t* d_nrows, in
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// px_filter_noalloc: the same filter for callers that cannot allocate device
+// memory, so cannot provide a workspace: e.g. code running under a host engine
+// whose memory manager owns every device byte and forbids side allocations, or a
+// serving loop that reserves all memory at start-up and must not call cudaMalloc
+// (which can synchronise the device) on its hot path. Its scratch (the status
+// word, the tile counter and one look-back state per tile) lives in the
+// file-scope device array below instead of a caller workspace.
+namespace px {
+namespace {
+
+constexpr int64_t kNoallocMaxTiles = 65536;  // PX_FILTER_NOALLOC_MAX_ROWS / kTile
+static_assert(PX_FILTER_NOALLOC_MAX_ROWS == kNoallocMaxTiles * kTile, "row limit must match the scratch size");
+// Header (status word) + scan scratch for the largest tile count, rounded like
+// scan_scratch_bytes: 256 + 524,544 = 524,800 bytes.
+constexpr size_t kNoallocScratchBytes = kWsScratch + ((16 + 8 * kNoallocMaxTiles + 255) / 256) * 256;
+
+// Held by every GPU that loads the library, until the process exits.
+static __device__ __align__(256) unsigned char g_filter_scratch[kNoallocScratchBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+void* g_noalloc_addr[kMaxDevices] = {};
+
+// Device address of g_filter_scratch on the current device. In host code the
+// array's name is only a host-side stand-in, so the address is looked up once per
+// device with cudaGetSymbolAddress (with that device current) and cached.
+px_status noalloc_scratch(void** out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return fail(PX_ERR_CUDA, "px_filter_noalloc: cudaGetDevice: %s", cudaGetErrorString(e));
+    if (dev < 0 || dev >= kMaxDevices) return fail(PX_ERR_UNSUPPORTED, "px_filter_noalloc: device %d", dev);
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_addr[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_filter_scratch);
+        if (e != cudaSuccess || !p)
+            return fail(PX_ERR_CUDA, "px_filter_noalloc: cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+        g_noalloc_addr[dev] = p;
+    }
+    *out = g_noalloc_addr[dev];
+    return PX_OK;
+}
+
+}  // namespace
+}  // namespace px
+
+extern "C" px_status px_filter_noalloc(const px_col* col, int64_t nrows, const int64_t* d_nrows, int64_t lo,
+                                       int64_t hi, int32_t* d_sel, int64_t* d_nsel, int32_t* d_status,
+                                       void* stream) {
+    set_error("");
+    px_status s = check_col(col, "px_filter_noalloc col", nrows == 0);
+    if (s != PX_OK) return s;
+    if (nrows < 0 || nrows > PX_FILTER_NOALLOC_MAX_ROWS)
+        return fail(PX_ERR_UNSUPPORTED, "px_filter_noalloc: nrows %lld outside [0, %lld]; use px_filter",
+                    (long long)nrows, (long long)PX_FILTER_NOALLOC_MAX_ROWS);
+    if (!d_sel || !d_nsel) return fail(PX_ERR_INVALID, "px_filter_noalloc: null d_sel or d_nsel");
+    void* scratch = nullptr;
+    if ((s = noalloc_scratch(&scratch)) != PX_OK) return s;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int64_t ntiles = cdiv(nrows, kTile);
+    if (kWsScratch + scan_scratch_bytes(ntiles) > kNoallocScratchBytes)
+        return fail(PX_ERR_UNSUPPORTED, "px_filter_noalloc: %lld tiles exceed the static scratch", (long long)ntiles);
+    // Each call clears the status word, the tile counter and the states it uses:
+    // the array keeps whatever the previous call left there.
+    cudaMemsetAsync(scratch, 0, kWsScratch + scan_scratch_bytes(ntiles), st);
+    if (nrows == 0) {
+        cudaMemsetAsync(d_nsel, 0, sizeof(int64_t), st);
+    } else {
+        const ScanScratch scan = scan_scratch(static_cast<char*>(scratch) + kWsScratch);
+        int32_t* status = &static_cast<WsHeader*>(scratch)->status;
+        const dim3 grid(static_cast<unsigned>(ntiles));
+        switch (col->type) {
+            case PX_I8:
+                filter_kernel<int8_t><<<grid, kThreads, 0, st>>>(static_cast<const int8_t*>(col->data), nrows,
+                                                                 d_nrows, lo, hi, d_sel, d_nsel, scan, status, ntiles);
+                break;
+            case PX_I32:
+                filter_kernel<int32_t><<<grid, kThreads, 0, st>>>(static_cast<const int32_t*>(col->data), nrows,
+                                                                  d_nrows, lo, hi, d_sel, d_nsel, scan, status,
+                                                                  ntiles);
+                break;
+            default:
+                filter_kernel<int64_t><<<grid, kThreads, 0, st>>>(static_cast<const int64_t*>(col->data), nrows,
+                                                                  d_nrows, lo, hi, d_sel, d_nsel, scan, status,
+                                                                  ntiles);
+                break;
+        }
+        note_launch();
+    }
+    if (d_status) cudaMemcpyAsync(d_status, scratch, sizeof(int32_t), cudaMemcpyDeviceToDevice, st);
+    return check_launch("px_filter_noalloc");
+}
