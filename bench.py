@@ -244,36 +244,12 @@ def run_px(args):
     stream = torch.cuda.current_stream()
 
     ops = list(alg_bytes(1, 1, 1).keys())
+    assert ops == AtScalePipeline.CALLS
 
     def step(ev=None):
         """One pass of the pipeline; ev: list of 7 events recorded between the calls."""
-        P, ws = pipe.nparts, pipe.ws
-        if ev:
-            ev[0].record(stream)
-        px.px_partition(pipe.dim, 0, P, pipe.seed, out=pipe.dparts, offsets=pipe.doff, ws=ws, stream=stream)
-        if ev:
-            ev[1].record(stream)
-        px.px_partition(pipe.fact, 0, P, pipe.seed, out=pipe.fparts, offsets=pipe.foff, ws=ws, stream=stream)
-        if ev:
-            ev[2].record(stream)
-        px.px_join_build(pipe.dparts, 0, seg=pipe.doff, unique=True, table=pipe.table, ws=ws, stream=stream)
-        if ev:
-            ev[3].record(stream)
-        j = px.px_join_probe(pipe.table, pipe.fparts, 0, seg=pipe.foff, carry=[1], payload=[pipe.dparts[1]],
-                             out=pipe.jout, out_cap=pipe.jout[0].numel(), out_seg=True, ws=ws, stream=stream)
-        if ev:
-            ev[4].record(stream)
-        part = px.px_groupby_agg(pipe.jout, [1], [(px.PX_SUM, 0, None), (px.PX_COUNT, None, None)],
-                                 max_groups=pipe.max_partial, seg=j["out_seg"], d_nrows=j["nout"], out=pipe.pout,
-                                 ws=ws, stream=stream)
-        if ev:
-            ev[5].record(stream)
-        fin = px.px_groupby_agg(pipe.pout, [0], [(px.PX_SUM, 1, None), (px.PX_SUM, 2, None)],
-                                max_groups=pipe.max_final, d_nrows=part["ngroups"], out=pipe.fout, ws=ws,
-                                stream=stream)
-        if ev:
-            ev[6].record(stream)
-        return part, fin
+        r = pipe.run(stream, mark=(lambda i: ev[i].record(stream)) if ev else None)
+        return r["partial"], r["final"]
 
     # correctness gate on this exact configuration before timing
     part, fin = step()

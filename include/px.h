@@ -229,6 +229,17 @@ px_status px_join_probe(const void* d_table, const px_batch* probe, int32_t fk_c
 
 size_t px_groupby_ws_bytes(int64_t nrows, int64_t max_groups);
 
+/* Optional column statistics for px_groupby_agg: key column k is expected (not
+ * required) to lie in [lo[k], hi[k]], as a query engine knows from its catalog or
+ * a dictionary. When the product of the ranges is small, each block aggregates
+ * into dense shared-memory arrays indexed by the key instead of a hash table.
+ * Rows outside the ranges are still aggregated exactly, through the hash path, so
+ * a wrong range costs speed, never correctness. */
+typedef struct {
+    int64_t lo[PX_MAX_KEYS];
+    int64_t hi[PX_MAX_KEYS];
+} px_key_range;
+
 /* GROUP BY the key columns key_cols[0..nkeys) (1..PX_MAX_KEYS columns of `in`)
  * over its positions (all rows or d_sel/d_nsel), computing aggs[0..naggs). With
  * nsegs > 0 groups are formed per segment (Partial aggregation per partition) and
@@ -237,12 +248,13 @@ size_t px_groupby_ws_bytes(int64_t nrows, int64_t max_groups);
  * columns, capacity out->nrows >= max_groups; groups come in an unspecified
  * order. *d_ngroups receives the number of groups; more than max_groups records
  * PX_ERR_CAPACITY. The sum of the key widths plus ceil(log2(nsegs)) bits must not
- * exceed 64 bits (PX_ERR_UNSUPPORTED otherwise). A Final merge of Partial results
- * is another px_groupby_agg over them with PX_SUM of each partial aggregate. */
+ * exceed 64 bits (PX_ERR_UNSUPPORTED otherwise). `range` (nullable) is the key
+ * statistic described above. A Final merge of Partial results is another
+ * px_groupby_agg over them with PX_SUM of each partial aggregate. */
 px_status px_groupby_agg(const px_batch* in, const int32_t* key_cols, int32_t nkeys,
                          const px_agg* aggs, int32_t naggs,
                          const int32_t* d_sel, const int64_t* d_nsel,
-                         const int64_t* d_seg, int32_t nsegs,
+                         const int64_t* d_seg, int32_t nsegs, const px_key_range* range,
                          int64_t max_groups, const px_batch* out, int32_t* d_out_seg,
                          int64_t* d_ngroups, void* d_ws, size_t ws_bytes, void* stream);
 

@@ -58,6 +58,10 @@ class px_agg(ctypes.Structure):
     _fields_ = [("op", ctypes.c_int32), ("a", ctypes.c_int32), ("b", ctypes.c_int32)]
 
 
+class px_key_range(ctypes.Structure):
+    _fields_ = [("lo", ctypes.c_int64 * 2), ("hi", ctypes.c_int64 * 2)]
+
+
 _lib = None
 
 
@@ -82,7 +86,8 @@ def _declare(lib):
         "px_join_probe_ws_bytes": ([I64], SZ),
         "px_join_probe": ([P, BP, I32, P, P, P, I32, P, I32, BP, BP, P, P, P, P, P, SZ, P], I32),
         "px_groupby_ws_bytes": ([I64, I64], SZ),
-        "px_groupby_agg": ([BP, P, I32, AP, I32, P, P, P, I32, I64, BP, P, P, P, SZ, P], I32),
+        "px_groupby_agg": ([BP, P, I32, AP, I32, P, P, P, I32, ctypes.POINTER(px_key_range), I64, BP, P, P, P,
+                            SZ, P], I32),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -299,9 +304,11 @@ def px_join_probe(table, cols, fk_col: int, *, sel=None, nsel=None, seg=None, d_
 
 
 def px_groupby_agg(cols, key_cols, aggs, *, max_groups: int, sel=None, nsel=None, seg=None, d_nrows=None,
-                   out=None, ws=None, stream=None):
+                   key_range=None, out=None, ws=None, stream=None):
     """GROUP BY key_cols computing aggs = [(op, a, b), ...] (HashAggregation, Sec. 3.2).
 
+    key_range: optional [(lo, hi), ...] per key column, a statistic of where the keys
+    lie (speed only; rows outside are still aggregated exactly).
     Returns a dict with 'keys' (list of key columns), 'aggs' (list of int64 columns),
     'seg' (int32 segment per group when segmented) and 'ngroups' (device int64[1]); the
     first ngroups rows are valid, in unspecified order."""
@@ -321,8 +328,14 @@ def px_groupby_agg(cols, key_cols, aggs, *, max_groups: int, sel=None, nsel=None
            "ngroups": torch.empty(1, dtype=torch.int64, device=dev)}
     if nsegs > 0:
         res["seg"] = torch.empty(max_groups, dtype=torch.int32, device=dev)
+    rng = None
+    if key_range is not None:
+        rng = px_key_range()
+        for k, (lo, hi) in enumerate(key_range):
+            rng.lo[k], rng.hi[k] = int(lo), int(hi)
     ws = _ws(ws, L.px_groupby_ws_bytes(n, max_groups), stream)
     _check(L.px_groupby_agg(inb.ref(), karr, len(key_cols), aarr, len(aggs), _sel_ptr(sel), _ptr(nsel), _ptr(seg),
-                            nsegs, max_groups, outb.ref(), _ptr(res.get("seg")), _ptr(res["ngroups"]), ws.ptr,
-                            ws.nbytes, _stream(stream)), "px_groupby_agg")
+                            nsegs, ctypes.byref(rng) if rng is not None else None, max_groups, outb.ref(),
+                            _ptr(res.get("seg")), _ptr(res["ngroups"]), ws.ptr, ws.nbytes, _stream(stream)),
+           "px_groupby_agg")
     return res

@@ -3,15 +3,24 @@
 //
 // Group key: the key columns (and the segment id) packed into one 64-bit code,
 // each key biased by its sign bit so the code orders like the signed tuple.
-// Each block is persistent over a contiguous range of positions and keeps a
-// shared-memory open-addressing table of (code -> 64-bit accumulators).
-// Rows of one warp that share a code are first combined with shuffles (peers from
+// Each block is persistent over a contiguous range of positions, which it walks
+// segment by segment. Per segment it aggregates into a block-local table and
+// merges that table into the global result when the segment ends (codes of a
+// finished segment never recur in the block's range, so the table starts empty
+// for the next one). The block-local table is either
+//   * dense: when the caller's key-range statistic makes the key space small,
+//     shared-memory arrays indexed by the key offset, replicated per warp when
+//     they fit (fewer same-address atomics); rows outside the range take the
+//     global path; or
+//   * hashed: an open-addressing shared-memory table (code -> accumulators);
+//     codes that find no room within a few probes take the global path.
+// Rows of one warp with equal codes are first combined with shuffles (peers from
 // match_any), so a hot key costs one shared-memory update per warp, not 32.
-// Codes that find no room in the block's table go to a global table in the
-// workspace; at the end every block merges its table into the global one. Global
-// slots are claimed with a CAS on a state word (empty -> claimed -> published),
-// take the next output row index from a counter, and accumulate with 64-bit
-// atomics straight into the output columns. All arithmetic is mod 2^64.
+// The global table lives in the workspace: slots are claimed with a CAS on a
+// state word (empty -> claimed -> published), take the next output row from a
+// counter, and accumulate with 64-bit atomics straight into the output columns.
+// All arithmetic is mod 2^64. Every thread loads all of its rows' inputs for a
+// tile before aggregating any of them, so each thread keeps many loads in flight.
 #include <algorithm>
 
 #include "px_common.cuh"
@@ -20,10 +29,12 @@ namespace px {
 namespace {
 
 constexpr int kThreads = 512;
-constexpr int kItems = 4;
+constexpr int kWarps = kThreads / 32;
+constexpr int kItems = 8;
 constexpr int kTile = kThreads * kItems;
-constexpr int kSmemProbes = 32;
-constexpr size_t kSmemBudget = 96 * 1024;
+constexpr int kSmemProbes = 8;
+constexpr int kMajority = 6;  // smallest group worth a warp reduction
+constexpr size_t kSmemBudget = 192 * 1024;
 
 struct Spec {
     int32_t nkeys, keybits, segbits, nsegs;
@@ -36,6 +47,24 @@ struct Spec {
     const void* a_in[PX_MAX_AGGS];
     const void* b_in[PX_MAX_AGGS];
     int64_t* agg_out[PX_MAX_AGGS];
+    // dense mode: per replica, SUM-like aggregates in u64 arrays [n64][D], COUNT
+    // aggregates in u32 arrays [n32][D] (a block counts < 2^32 rows per segment),
+    // then an occupancy bitmap when there is no COUNT.
+    int32_t dense;      // 1: dense block arrays
+    int32_t reps;       // replicas: kThreads (one per thread, plain adds) or 1..kWarps (warp w: w % reps)
+    int32_t count_agg;  // a COUNT aggregate marks occupancy; -1: use the bitmap
+    uint32_t D;         // dense slots per replica
+    int32_t n64, n32;
+    int32_t kind[PX_MAX_AGGS];  // 0: u64 array, 1: u32 array
+    int32_t slot[PX_MAX_AGGS];  // index of the aggregate's array within its kind
+    uint32_t rep_bytes;         // bytes per replica
+    int64_t lo[PX_MAX_KEYS];
+    uint64_t span[PX_MAX_KEYS];
+    // dense global result (when the whole (segment, key) space fits max_groups)
+    int32_t dglobal;
+    uint64_t E;                   // entries: max(nsegs, 1) * D
+    unsigned long long* dg_acc;   // [naggs][E]
+    uint32_t* dg_occ;             // [ceil(E / 32)] occupancy bits (only without COUNT)
 };
 
 struct GTable {
@@ -54,13 +83,13 @@ __device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t* p) {
 
 __device__ __forceinline__ uint64_t bits_mask(int bits) { return bits >= 64 ? ~0ull : ((1ull << bits) - 1); }
 
-__device__ __forceinline__ uint64_t encode(const Spec& sp, int64_t row, int q) {
-    uint64_t code = 0;
-    for (int k = 0; k < sp.nkeys; ++k) {
-        const int bits = 8 * sp.key_w[k];
-        const uint64_t u = (static_cast<uint64_t>(load_int(sp.key_in[k], sp.key_w[k], row)) ^ (1ull << (bits - 1))) &
-                           bits_mask(bits);
-        code = bits >= 64 ? u : ((code << bits) | u);
+// Group code of key values k0 (, k1) (sign-extended) in segment q.
+__device__ __forceinline__ uint64_t compose(const Spec& sp, int64_t k0, int64_t k1, int q) {
+    const int b0 = 8 * sp.key_w[0];
+    uint64_t code = (static_cast<uint64_t>(k0) ^ (1ull << (b0 - 1))) & bits_mask(b0);
+    if (sp.nkeys > 1) {
+        const int b1 = 8 * sp.key_w[1];
+        code = (code << b1) | ((static_cast<uint64_t>(k1) ^ (1ull << (b1 - 1))) & bits_mask(b1));
     }
     if (sp.segbits) code |= static_cast<uint64_t>(q) << sp.keybits;
     return code;
@@ -74,8 +103,7 @@ __device__ __forceinline__ void write_group(const Spec& sp, uint64_t code, int32
         const uint64_t u = (code >> shift) & bits_mask(bits);
         // u = raw ^ sb; sign-extending raw is (raw ^ sb) - sb = u - sb.
         const uint64_t sb = 1ull << (bits - 1);
-        const int64_t v = static_cast<int64_t>(u - sb);
-        store_int(sp.key_out[k], sp.key_w[k], gi, v);
+        store_int(sp.key_out[k], sp.key_w[k], gi, static_cast<int64_t>(u - sb));
     }
     if (out_seg) out_seg[gi] = sp.segbits ? static_cast<int32_t>(code >> sp.keybits) : 0;
 }
@@ -99,6 +127,9 @@ __device__ int32_t global_group(const GTable& g, const Spec& sp, uint64_t code, 
                 atomicExch(&g.state[s], 2u);
                 return gi;
             }
+            // The CAS lost to another claimer; it carries no acquire ordering, so
+            // read the state again with one before trusting key and gidx.
+            st = ld_acquire_u32(&g.state[s]);
         }
         uint32_t spins = 0;
         while (st == 1) {
@@ -124,8 +155,8 @@ __device__ __forceinline__ void global_add(const GTable& g, const Spec& sp, uint
         atomicAdd(reinterpret_cast<unsigned long long*>(&sp.agg_out[a][gi]), static_cast<unsigned long long>(v[a]));
 }
 
-// Slot of `code` in the block's table, inserting it if absent; -1 if no room
-// within kSmemProbes probes.
+// Slot of `code` in the block's hash table, inserting it if absent; -1 if no
+// room within kSmemProbes probes.
 __device__ __forceinline__ int smem_slot(uint32_t* s_state, unsigned long long* s_key, uint32_t smask, uint64_t code,
                                          int32_t* status) {
     uint32_t s = static_cast<uint32_t>(fmix64(code)) & smask;
@@ -156,86 +187,444 @@ __device__ __forceinline__ int smem_slot(uint32_t* s_state, unsigned long long* 
     return -1;
 }
 
+struct Smem {
+    // dense: replicas of rep_bytes each (see Spec)
+    unsigned char* rep0;
+    uint32_t occ_words;
+    // hashed: low words [naggs][S], high words [naggs][S], key[S], state[S]
+    uint32_t* h_lo;
+    uint32_t* h_hi;
+    unsigned long long* h_key;
+    uint32_t* h_state;
+    uint32_t S;
+};
+
+// A replica holds each 64-bit sum as two 32-bit words, low words [n64][D] then
+// high words [n64][D], so every update is a native 32-bit shared atomic: a 64-bit
+// shared atomicAdd retries under contention and collapses on hot keys.
+__device__ __forceinline__ uint32_t* rep_lo(const Spec& sp, const Smem& m, int r) {
+    return reinterpret_cast<uint32_t*>(m.rep0 + static_cast<size_t>(r) * sp.rep_bytes);
+}
+__device__ __forceinline__ uint32_t* rep_hi(const Spec& sp, const Smem& m, int r) {
+    return rep_lo(sp, m, r) + static_cast<size_t>(sp.n64) * sp.D;
+}
+__device__ __forceinline__ uint32_t* rep_u32(const Spec& sp, const Smem& m, int r) {
+    return rep_lo(sp, m, r) + 2 * static_cast<size_t>(sp.n64) * sp.D;
+}
+
+// Adds x (mod 2^64) to the 64-bit value held as words lo/hi: the returned old low
+// word tells whether the low addition wrapped; the high word changes only when x
+// has high bits or the low word carried. Exact once all updates have landed.
+__device__ __forceinline__ void add_split_atomic(uint32_t* lo, uint32_t* hi, uint64_t x) {
+    const uint32_t xl = static_cast<uint32_t>(x), xh = static_cast<uint32_t>(x >> 32);
+    const uint32_t old = atomicAdd(lo, xl);
+    const uint32_t add_hi = xh + (old + xl < old ? 1u : 0u);
+    if (add_hi) atomicAdd(hi, add_hi);
+}
+__device__ __forceinline__ void add_split(uint32_t* lo, uint32_t* hi, uint64_t x) {
+    const uint32_t xl = static_cast<uint32_t>(x), old = *lo;
+    *lo = old + xl;
+    *hi += static_cast<uint32_t>(x >> 32) + (old + xl < old ? 1u : 0u);
+}
+__device__ __forceinline__ uint32_t* rep_occ(const Spec& sp, const Smem& m, int r) {
+    return rep_u32(sp, m, r) + static_cast<size_t>(sp.n32) * sp.D;
+}
+
+__device__ __forceinline__ void clear_block_table(const Spec& sp, const Smem& m) {
+    if (sp.dense) {
+        uint32_t* w = reinterpret_cast<uint32_t*>(m.rep0);
+        const uint32_t nw = static_cast<uint32_t>(sp.reps) * sp.rep_bytes / 4;
+        for (uint32_t i = threadIdx.x; i < nw; i += kThreads) w[i] = 0;
+    } else {
+        for (uint32_t s = threadIdx.x; s < m.S; s += kThreads) m.h_state[s] = 0;
+        for (uint32_t s = threadIdx.x; s < m.S * sp.naggs; s += kThreads) m.h_lo[s] = m.h_hi[s] = 0;
+    }
+}
+
+// Merge the block table (segment q) into the global table and clear it.
+__device__ void flush_block_table(const Spec& sp, const Smem& m, int q, const GTable& g, int64_t max_groups,
+                                  int32_t* out_seg, int32_t* status) {
+    __syncthreads();
+    if (sp.dense) {
+        for (uint32_t d = threadIdx.x; d < sp.D; d += kThreads) {
+            uint64_t v[PX_MAX_AGGS];
+            bool occ = false;
+            for (int a = 0; a < sp.naggs; ++a) v[a] = 0;
+            for (int r = 0; r < sp.reps; ++r) {
+                uint32_t* LO = rep_lo(sp, m, r);
+                uint32_t* HI = rep_hi(sp, m, r);
+                uint32_t* A32 = rep_u32(sp, m, r);
+                for (int a = 0; a < sp.naggs; ++a) {
+                    if (sp.kind[a] == 0) {
+                        const size_t o = static_cast<size_t>(sp.slot[a]) * sp.D + d;
+                        v[a] += (static_cast<uint64_t>(HI[o]) << 32) | LO[o];
+                        LO[o] = 0;
+                        HI[o] = 0;
+                    } else {
+                        uint32_t* p = &A32[static_cast<size_t>(sp.slot[a]) * sp.D + d];
+                        v[a] += *p;
+                        *p = 0;
+                    }
+                }
+                if (sp.count_agg < 0) occ |= ((rep_occ(sp, m, r)[d / 32] >> (d % 32)) & 1u) != 0;
+            }
+            if (sp.count_agg >= 0) occ = v[sp.count_agg] != 0;
+            if (!occ) continue;
+            if (sp.dglobal) {
+                // Dense global array: entry (segment q, slot d); no hashing, no claim.
+                const uint64_t e = static_cast<uint64_t>(q) * sp.D + d;
+                for (int a = 0; a < sp.naggs; ++a)
+                    atomicAdd(&sp.dg_acc[a * sp.E + e], static_cast<unsigned long long>(v[a]));
+                if (sp.count_agg < 0) atomicOr(&sp.dg_occ[e / 32], 1u << (e % 32));
+                continue;
+            }
+            const int64_t k0 = sp.lo[0] + static_cast<int64_t>(d / sp.span[1]);
+            const int64_t k1 = sp.nkeys > 1 ? sp.lo[1] + static_cast<int64_t>(d % sp.span[1]) : 0;
+            global_add(g, sp, compose(sp, k0, k1, q), v, max_groups, out_seg, status);
+        }
+        __syncthreads();
+        if (sp.count_agg < 0)
+            for (uint32_t i = threadIdx.x; i < sp.reps * m.occ_words; i += kThreads)
+                rep_occ(sp, m, i / m.occ_words)[i % m.occ_words] = 0;
+    } else {
+        for (uint32_t s = threadIdx.x; s < m.S; s += kThreads) {
+            if (m.h_state[s] == 2) {
+                uint64_t v[PX_MAX_AGGS];
+                for (int a = 0; a < sp.naggs; ++a) {
+                    const size_t o = static_cast<size_t>(a) * m.S + s;
+                    v[a] = (static_cast<uint64_t>(m.h_hi[o]) << 32) | m.h_lo[o];
+                    m.h_lo[o] = m.h_hi[o] = 0;
+                }
+                global_add(g, sp, m.h_key[s], v, max_groups, out_seg, status);
+            }
+            m.h_state[s] = 0;
+        }
+    }
+    __syncthreads();
+}
+
+constexpr uint32_t kIdxNone = 0xffffffffu;   // no row at this item
+constexpr uint32_t kIdxOutside = 0xfffffffeu;  // key outside the dense range
+
+// v[i] = column value at row[i] (sign-extended), 0 where row[i] < 0. One type
+// switch per column, then kItems independent loads.
+template <typename T>
+__device__ __forceinline__ void load_col_t(const void* p, const int32_t* row, int64_t* v) {
+#pragma unroll
+    for (int i = 0; i < kItems; ++i) v[i] = row[i] >= 0 ? static_cast<int64_t>(static_cast<const T*>(p)[row[i]]) : 0;
+}
+__device__ __forceinline__ void load_col(const void* p, int w, const int32_t* row, int64_t* v) {
+    if (w == 8) load_col_t<int64_t>(p, row, v);
+    else if (w == 4) load_col_t<int32_t>(p, row, v);
+    else load_col_t<int8_t>(p, row, v);
+}
+
+// Dense-mode aggregation of positions [a0, a1) of segment q: keys become slot
+// indices at load time, each aggregate is applied with one atomic per row (or a
+// plain add into the thread's private replica), rows outside the key range take
+// the global path afterwards.
+template <int NA>
+__device__ void aggregate_range_dense(const Spec& sp, const Smem& m, const int32_t* __restrict__ sel, int64_t a0,
+                                      int64_t a1, int q, const GTable& g, int64_t max_groups, int32_t* out_seg,
+                                      int32_t* status) {
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const bool private_rep = sp.reps == kThreads;
+    const int rep = private_rep ? tid : warp % sp.reps;
+    uint32_t* const LO = rep_lo(sp, m, rep);
+    uint32_t* const HI = rep_hi(sp, m, rep);
+    uint32_t* const A32 = rep_u32(sp, m, rep);
+    uint32_t* const OCC = rep_occ(sp, m, rep);
+    for (int64_t tb = a0; tb < a1; tb += kTile) {
+        int32_t row[kItems];
+        uint32_t idx[kItems];
+#pragma unroll
+        for (int i = 0; i < kItems; ++i) {
+            const int64_t j = tb + i * kThreads + tid;
+            row[i] = j < a1 ? (sel ? sel[j] : static_cast<int32_t>(j)) : -1;
+        }
+        {
+            int64_t k0[kItems], k1[kItems];
+            load_col(sp.key_in[0], sp.key_w[0], row, k0);
+            if (sp.nkeys > 1) load_col(sp.key_in[1], sp.key_w[1], row, k1);
+#pragma unroll
+            for (int i = 0; i < kItems; ++i) {
+                const uint64_t o0 = static_cast<uint64_t>(k0[i] - sp.lo[0]);
+                const uint64_t o1 = sp.nkeys > 1 ? static_cast<uint64_t>(k1[i] - sp.lo[1]) : 0;
+                idx[i] = row[i] < 0 ? kIdxNone
+                                    : ((o0 < sp.span[0] && o1 < sp.span[1]) ? static_cast<uint32_t>(o0 * sp.span[1] + o1)
+                                                                            : kIdxOutside);
+            }
+        }
+        int64_t v[NA > 0 ? NA : 1][kItems];
+#pragma unroll
+        for (int a = 0; a < NA; ++a) {
+            if (a >= sp.naggs) break;
+            if (sp.op[a] == PX_COUNT) {
+#pragma unroll
+                for (int i = 0; i < kItems; ++i) v[a][i] = 1;
+            } else {
+                load_col(sp.a_in[a], sp.a_w[a], row, v[a]);
+                if (sp.op[a] == PX_SUM_MUL) {
+                    int64_t y[kItems];
+                    load_col(sp.b_in[a], sp.b_w[a], row, y);
+#pragma unroll
+                    for (int i = 0; i < kItems; ++i)
+                        v[a][i] = static_cast<int64_t>(static_cast<uint64_t>(v[a][i]) * static_cast<uint64_t>(y[i]));
+                }
+            }
+        }
+        // Hot keys: when lane 0's slot is shared by at least kMajority lanes, those
+        // rows are summed with a butterfly and lane 0 applies them once (many lanes
+        // on one address would serialise the shared-memory atomics).
+        uint32_t apply[kItems];
+#pragma unroll
+        for (int i = 0; i < kItems; ++i) {
+            apply[i] = idx[i];
+            if (private_rep) continue;
+            const uint32_t c0 = __shfl_sync(FULL, idx[i], 0);
+            const uint32_t mm = __ballot_sync(FULL, idx[i] == c0);
+            if (c0 < kIdxOutside && __popc(mm) >= kMajority) {
+                const bool in = (mm >> lane) & 1u;
+#pragma unroll
+                for (int a = 0; a < NA; ++a) {
+                    if (a >= sp.naggs) break;
+                    const int64_t x = warp_sum(in ? v[a][i] : int64_t(0));
+                    if (lane == 0) v[a][i] = x;
+                }
+                if (in && lane != 0) apply[i] = kIdxNone;
+            }
+        }
+        // Apply in-range rows.
+#pragma unroll
+        for (int a = 0; a < NA; ++a) {
+            if (a >= sp.naggs) break;
+            const size_t off = static_cast<size_t>(sp.slot[a]) * sp.D;
+            if (sp.kind[a] == 0) {
+#pragma unroll
+                for (int i = 0; i < kItems; ++i) {
+                    if (apply[i] >= kIdxOutside) continue;
+                    if (private_rep) add_split(&LO[off + apply[i]], &HI[off + apply[i]], static_cast<uint64_t>(v[a][i]));
+                    else add_split_atomic(&LO[off + apply[i]], &HI[off + apply[i]], static_cast<uint64_t>(v[a][i]));
+                }
+            } else {
+#pragma unroll
+                for (int i = 0; i < kItems; ++i) {
+                    if (apply[i] >= kIdxOutside) continue;
+                    if (private_rep) A32[off + apply[i]] += static_cast<uint32_t>(v[a][i]);
+                    else atomicAdd(&A32[off + apply[i]], static_cast<uint32_t>(v[a][i]));
+                }
+            }
+        }
+        if (sp.count_agg < 0) {
+#pragma unroll
+            for (int i = 0; i < kItems; ++i) {
+                if (apply[i] >= kIdxOutside) continue;
+                if (private_rep) OCC[apply[i] / 32] |= 1u << (apply[i] % 32);
+                else atomicOr(&OCC[apply[i] / 32], 1u << (apply[i] % 32));
+            }
+        }
+        // Rows outside the key range (rare when the statistic is right): global path.
+#pragma unroll
+        for (int i = 0; i < kItems; ++i) {
+            if (idx[i] != kIdxOutside) continue;
+            const int64_t r = row[i];
+            const int64_t k0 = load_int(sp.key_in[0], sp.key_w[0], r);
+            const int64_t k1 = sp.nkeys > 1 ? load_int(sp.key_in[1], sp.key_w[1], r) : 0;
+            uint64_t full[PX_MAX_AGGS];
+#pragma unroll
+            for (int a = 0; a < NA; ++a) full[a] = static_cast<uint64_t>(v[a][i]);
+            global_add(g, sp, compose(sp, k0, k1, q), full, max_groups, out_seg, status);
+        }
+    }
+}
+
+// Hash-mode aggregation of positions [a0, a1) of segment q into the block's
+// shared-memory hash table; codes that find no room go to the global table. NA:
+// number of aggregates when known at compile time (0..4), or PX_MAX_AGGS.
+template <int NA>
+__device__ void aggregate_range(const Spec& sp, const Smem& m, const int32_t* __restrict__ sel, int64_t a0, int64_t a1,
+                                int q, const GTable& g, int64_t max_groups, int32_t* out_seg, int32_t* status) {
+    const int tid = threadIdx.x, lane = tid & 31;
+    for (int64_t tb = a0; tb < a1; tb += kTile) {
+        int32_t row[kItems];
+#pragma unroll
+        for (int i = 0; i < kItems; ++i) {
+            const int64_t j = tb + i * kThreads + tid;
+            row[i] = j < a1 ? (sel ? sel[j] : static_cast<int32_t>(j)) : -1;
+        }
+        uint64_t code[kItems];
+        {
+            int64_t k0[kItems], k1[kItems];
+            load_col(sp.key_in[0], sp.key_w[0], row, k0);
+            if (sp.nkeys > 1) load_col(sp.key_in[1], sp.key_w[1], row, k1);
+#pragma unroll
+            for (int i = 0; i < kItems; ++i) code[i] = compose(sp, k0[i], sp.nkeys > 1 ? k1[i] : 0, q);
+        }
+        int64_t v[NA > 0 ? NA : 1][kItems];
+#pragma unroll
+        for (int a = 0; a < NA; ++a) {
+            if (a >= sp.naggs) break;
+            if (sp.op[a] == PX_COUNT) {
+#pragma unroll
+                for (int i = 0; i < kItems; ++i) v[a][i] = 1;
+            } else {
+                load_col(sp.a_in[a], sp.a_w[a], row, v[a]);
+                if (sp.op[a] == PX_SUM_MUL) {
+                    int64_t y[kItems];
+                    load_col(sp.b_in[a], sp.b_w[a], row, y);
+#pragma unroll
+                    for (int i = 0; i < kItems; ++i)
+                        v[a][i] = static_cast<int64_t>(static_cast<uint64_t>(v[a][i]) * static_cast<uint64_t>(y[i]));
+                }
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < kItems; ++i) {
+            const bool valid = row[i] >= 0;
+            // Hot keys: lane 0's code shared by >= kMajority lanes is summed with a
+            // butterfly and applied once by lane 0.
+            bool lead = valid;
+            const uint64_t c0 = __shfl_sync(FULL, code[i], 0);
+            const uint32_t mm = __ballot_sync(FULL, valid && code[i] == c0);
+            if ((mm & 1u) && __popc(mm) >= kMajority) {
+                const bool in = (mm >> lane) & 1u;
+#pragma unroll
+                for (int a = 0; a < NA; ++a) {
+                    if (a >= sp.naggs) break;
+                    const int64_t x = warp_sum(in ? v[a][i] : int64_t(0));
+                    if (lane == 0) v[a][i] = x;
+                }
+                lead = valid && (!in || lane == 0);
+            }
+            if (!lead) continue;
+            const int s = smem_slot(m.h_state, m.h_key, m.S - 1, code[i], status);
+            if (s >= 0) {
+#pragma unroll
+                for (int a = 0; a < NA; ++a) {
+                    if (a >= sp.naggs) break;
+                    const size_t o = static_cast<size_t>(a) * m.S + s;
+                    add_split_atomic(&m.h_lo[o], &m.h_hi[o], static_cast<uint64_t>(v[a][i]));
+                }
+            } else {
+                uint64_t full[PX_MAX_AGGS];
+#pragma unroll
+                for (int a = 0; a < NA; ++a) full[a] = static_cast<uint64_t>(v[a][i]);
+                global_add(g, sp, code[i], full, max_groups, out_seg, status);
+            }
+        }
+    }
+}
+
+// DENSE must equal sp.dense: the two modes are separate kernels so each gets its
+// own register allocation.
+template <int NA, bool DENSE>
 __global__ void __launch_bounds__(kThreads)
 groupby_kernel(Spec sp, const int32_t* __restrict__ sel, const int64_t* __restrict__ d_n, int64_t ncap,
                const int64_t* __restrict__ d_seg, GTable g, int64_t max_groups, int32_t* __restrict__ out_seg,
-               int32_t* status, uint32_t sslots) {
+               int32_t* status, uint32_t hash_slots) {
     extern __shared__ __align__(16) unsigned char smem[];
-    unsigned long long* s_acc = reinterpret_cast<unsigned long long*>(smem);      // naggs x sslots
-    unsigned long long* s_key = s_acc + static_cast<size_t>(sp.naggs) * sslots;  // sslots
-    uint32_t* s_state = reinterpret_cast<uint32_t*>(s_key + sslots);             // sslots
-    const uint32_t smask = sslots - 1;
-    const int tid = threadIdx.x, lane = tid & 31;
-    for (uint32_t s = tid; s < sslots; s += kThreads) s_state[s] = 0;
-    for (uint32_t s = tid; s < sslots * sp.naggs; s += kThreads) s_acc[s] = 0;
+    Smem m;
+    if (DENSE) {
+        m.rep0 = smem;
+        m.occ_words = (sp.D + 31) / 32;
+    } else {
+        m.S = hash_slots;
+        m.h_lo = reinterpret_cast<uint32_t*>(smem);
+        m.h_hi = m.h_lo + static_cast<size_t>(sp.naggs) * hash_slots;
+        m.h_key = reinterpret_cast<unsigned long long*>(m.h_hi + static_cast<size_t>(sp.naggs) * hash_slots);
+        m.h_state = reinterpret_cast<uint32_t*>(m.h_key + hash_slots);
+    }
+    clear_block_table(sp, m);
     __syncthreads();
 
     const int64_t n = actual_rows(d_n, ncap);
     const int64_t chunk = cdiv(cdiv(n, gridDim.x), kTile) * kTile;
     const int64_t cb = static_cast<int64_t>(blockIdx.x) * chunk;
     const int64_t ce = n < cb + chunk ? n : cb + chunk;
-    for (int64_t tb = cb; tb < ce; tb += kTile) {
-#pragma unroll 1
-        for (int i = 0; i < kItems; ++i) {
-            const int64_t j = tb + i * kThreads + tid;
-            const bool valid = j < ce;
-            uint64_t code = 0;
-            uint64_t v[PX_MAX_AGGS];
-            for (int a = 0; a < PX_MAX_AGGS; ++a) v[a] = 0;
-            if (valid) {
-                const int64_t r = sel ? static_cast<int64_t>(sel[j]) : j;
-                const int q = sp.nsegs > 1 ? seg_of(d_seg, sp.nsegs, j) : 0;
-                code = encode(sp, r, q);
-                for (int a = 0; a < sp.naggs; ++a) {
-                    if (sp.op[a] == PX_COUNT) {
-                        v[a] = 1;
-                    } else {
-                        const uint64_t x = static_cast<uint64_t>(load_int(sp.a_in[a], sp.a_w[a], r));
-                        v[a] = sp.op[a] == PX_SUM ? x
-                                                  : x * static_cast<uint64_t>(load_int(sp.b_in[a], sp.b_w[a], r));
-                    }
-                }
+    int64_t pos = cb;
+    while (pos < ce) {
+        int q = 0;
+        int64_t qend = ce;
+        if (sp.nsegs > 1) {
+            q = seg_of(d_seg, sp.nsegs, pos);
+            if (q + 1 < sp.nsegs) {
+                const int64_t e = d_seg[q + 1];
+                if (e > pos && e < ce) qend = e;
             }
-            const uint32_t vmask = __ballot_sync(FULL, valid);
-            if (vmask == 0) continue;
-            const uint32_t peers = __match_any_sync(FULL, code) & vmask;
-            bool lead;
-            if (vmask == FULL && peers == FULL) {
-                // Whole warp on one group: butterfly reduction, lane 0 updates.
-                for (int a = 0; a < sp.naggs; ++a) v[a] = warp_sum(v[a]);
-                lead = (lane == 0);
-            } else {
-                // Each group's lowest lane gathers its peers' values.
-                const int leader = valid ? __ffs(peers) - 1 : -1;
-                lead = valid && lane == leader;
-                uint32_t rest = lead ? (peers & ~(1u << lane)) : 0u;
-                const int maxc = __reduce_max_sync(FULL, valid ? __popc(peers) : 0);
-                for (int it = 1; it < maxc; ++it) {
-                    const int src = rest ? __ffs(rest) - 1 : lane;
-                    for (int a = 0; a < sp.naggs; ++a) {
-                        const uint64_t x = __shfl_sync(FULL, v[a], src);
-                        if (rest) v[a] += x;
-                    }
-                    if (rest) rest &= rest - 1;
-                }
-            }
-            if (lead) {
-                const int s = smem_slot(s_state, s_key, smask, code, status);
-                if (s >= 0) {
-                    for (int a = 0; a < sp.naggs; ++a) atomicAdd(&s_acc[static_cast<size_t>(a) * sslots + s], v[a]);
-                } else {
-                    global_add(g, sp, code, v, max_groups, out_seg, status);
-                }
+        }
+        if (DENSE) aggregate_range_dense<NA>(sp, m, sel, pos, qend, q, g, max_groups, out_seg, status);
+        else aggregate_range<NA>(sp, m, sel, pos, qend, q, g, max_groups, out_seg, status);
+        flush_block_table(sp, m, q, g, max_groups, out_seg, status);
+        pos = qend;
+    }
+}
+
+constexpr int kEmitThreads = 256;
+constexpr int kEmitItems = 8;
+constexpr int kEmitTile = kEmitThreads * kEmitItems;
+constexpr int kEmitWarps = kEmitThreads / 32;
+
+// Writes the occupied entries of the dense global array as output groups, in
+// (segment, key) order, after the groups the hash path claimed (rows whose keys
+// fell outside the key range). Single pass with a bounded look-back.
+__global__ void __launch_bounds__(kEmitThreads)
+dense_emit_kernel(Spec sp, const unsigned long long* __restrict__ ngroups_hash, int64_t max_groups,
+                  int32_t* __restrict__ out_seg, int64_t* __restrict__ d_ngroups, ScanScratch scan, int32_t* status,
+                  int64_t ntiles) {
+    __shared__ int64_t s_tile;
+    __shared__ int64_t s_excl;
+    __shared__ int32_t s_warp[kEmitWarps];
+    const int64_t tile = next_tile(scan.counter, &s_tile);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t base = tile * kEmitTile + warp * (32 * kEmitItems);
+    const int64_t E = static_cast<int64_t>(sp.E);
+    const int64_t first = static_cast<int64_t>(*ngroups_hash);
+    uint32_t mask[kEmitItems];
+    int32_t cnt = 0;
+#pragma unroll
+    for (int i = 0; i < kEmitItems; ++i) {
+        const int64_t e = base + i * 32 + lane;
+        bool occ = false;
+        if (e < E)
+            occ = sp.count_agg >= 0 ? sp.dg_acc[sp.count_agg * E + e] != 0 : ((sp.dg_occ[e / 32] >> (e % 32)) & 1u);
+        mask[i] = __ballot_sync(FULL, occ);
+        cnt += __popc(mask[i]);
+    }
+    if (lane == 0) s_warp[warp] = cnt;
+    __syncthreads();
+    if (warp == 0) {
+        const int32_t w = lane < kEmitWarps ? s_warp[lane] : 0;
+        const int32_t incl = warp_incl_scan(w);
+        const int32_t total = __shfl_sync(FULL, incl, 31);
+        if (lane < kEmitWarps) s_warp[lane] = incl - w;
+        const int64_t excl = lookback(scan.states, tile, total, status);
+        if (lane == 0) {
+            s_excl = excl;
+            if (tile == ntiles - 1) {
+                *d_ngroups = first + excl + total;
+                if (first + excl + total > max_groups) set_status(status, PX_ERR_CAPACITY);
             }
         }
     }
     __syncthreads();
-    // Merge this block's table into the global one.
-    for (uint32_t s = tid; s < sslots; s += kThreads) {
-        if (s_state[s] != 2) continue;
-        uint64_t v[PX_MAX_AGGS];
-        for (int a = 0; a < sp.naggs; ++a) v[a] = s_acc[static_cast<size_t>(a) * sslots + s];
-        global_add(g, sp, s_key[s], v, max_groups, out_seg, status);
+    int64_t pos = first + s_excl + s_warp[warp];
+    const uint32_t lt = lanemask_lt();
+#pragma unroll
+    for (int i = 0; i < kEmitItems; ++i) {
+        if (mask[i] & (1u << lane)) {
+            const int64_t e = base + i * 32 + lane;
+            const int64_t p = pos + __popc(mask[i] & lt);
+            if (p < max_groups) {
+                const uint64_t q = static_cast<uint64_t>(e) / sp.D;
+                const uint64_t d = static_cast<uint64_t>(e) % sp.D;
+                store_int(sp.key_out[0], sp.key_w[0], p, sp.lo[0] + static_cast<int64_t>(d / sp.span[1]));
+                if (sp.nkeys > 1)
+                    store_int(sp.key_out[1], sp.key_w[1], p, sp.lo[1] + static_cast<int64_t>(d % sp.span[1]));
+                if (out_seg) out_seg[p] = static_cast<int32_t>(q);
+                for (int a = 0; a < sp.naggs; ++a) sp.agg_out[a][p] = static_cast<int64_t>(sp.dg_acc[a * E + e]);
+            }
+        }
+        pos += __popc(mask[i]);
     }
 }
 
@@ -245,7 +634,7 @@ uint32_t gtable_slots(int64_t max_groups) {
     return static_cast<uint32_t>(G);
 }
 
-uint32_t smem_slots(int naggs) {
+uint32_t hash_slots(int naggs) {
     uint32_t s = 8192;
     while (s > 64 && static_cast<size_t>(s) * (12 + 8 * static_cast<size_t>(naggs)) > kSmemBudget) s >>= 1;
     return s;
@@ -258,6 +647,30 @@ int num_sms() {
     return n > 0 ? n : 1;
 }
 
+template <int NA, bool DENSE>
+px_status launch_mode(const Spec& sp, size_t smem, const int32_t* sel, const int64_t* d_n, int64_t ncap,
+                      const int64_t* d_seg, const GTable& g, int64_t max_groups, int32_t* out_seg, int32_t* status,
+                      uint32_t hslots, cudaStream_t st) {
+    auto kernel = groupby_kernel<NA, DENSE>;
+    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, smem);
+    const int64_t grid = std::max<int64_t>(
+        1, std::min<int64_t>(cdiv(ncap, kTile), static_cast<int64_t>(num_sms()) * std::max(1, per_sm)));
+    kernel<<<static_cast<unsigned>(grid), kThreads, smem, st>>>(sp, sel, d_n, ncap, d_seg, g, max_groups, out_seg,
+                                                                status, hslots);
+    note_launch();
+    return check_launch("px_groupby_agg");
+}
+
+template <int NA>
+px_status launch(const Spec& sp, size_t smem, const int32_t* sel, const int64_t* d_n, int64_t ncap,
+                 const int64_t* d_seg, const GTable& g, int64_t max_groups, int32_t* out_seg, int32_t* status,
+                 uint32_t hslots, cudaStream_t st) {
+    if (sp.dense) return launch_mode<NA, true>(sp, smem, sel, d_n, ncap, d_seg, g, max_groups, out_seg, status, hslots, st);
+    return launch_mode<NA, false>(sp, smem, sel, d_n, ncap, d_seg, g, max_groups, out_seg, status, hslots, st);
+}
+
 }  // namespace
 }  // namespace px
 
@@ -265,17 +678,37 @@ using namespace px;
 
 extern "C" {
 
-size_t px_groupby_ws_bytes(int64_t nrows, int64_t max_groups) {
-    (void)nrows;
+// Workspace: [header][group counter][hash table: state, key, gidx (G slots)]
+// [dense global: acc (PX_MAX_AGGS x max_groups), occupancy bits][emit scan scratch].
+struct WsLayout {
+    size_t counter, state, key, gidx, dg_acc, dg_occ, emit_scan, total;
+};
+
+WsLayout ws_layout(int64_t max_groups) {
     if (max_groups < 1) max_groups = 1;
     const size_t G = gtable_slots(max_groups);
-    return kWsScratch + 256 + align_up(4 * G, 256) + align_up(8 * G, 256) + align_up(4 * G, 256);
+    const size_t M = static_cast<size_t>(max_groups);
+    WsLayout L;
+    L.counter = kWsScratch;
+    L.state = L.counter + 256;
+    L.key = L.state + align_up(4 * G, 256);
+    L.gidx = L.key + align_up(8 * G, 256);
+    L.dg_acc = L.gidx + align_up(4 * G, 256);
+    L.dg_occ = L.dg_acc + align_up(8 * PX_MAX_AGGS * M, 256);
+    L.emit_scan = L.dg_occ + align_up((M + 31) / 32 * 4, 256);
+    L.total = L.emit_scan + scan_scratch_bytes(cdiv(static_cast<int64_t>(M), kEmitTile));
+    return L;
+}
+
+size_t px_groupby_ws_bytes(int64_t nrows, int64_t max_groups) {
+    (void)nrows;
+    return ws_layout(max_groups).total;
 }
 
 px_status px_groupby_agg(const px_batch* in, const int32_t* key_cols, int32_t nkeys, const px_agg* aggs,
                          int32_t naggs, const int32_t* d_sel, const int64_t* d_nsel, const int64_t* d_seg,
-                         int32_t nsegs, int64_t max_groups, const px_batch* out, int32_t* d_out_seg,
-                         int64_t* d_ngroups, void* d_ws, size_t ws_bytes, void* stream) {
+                         int32_t nsegs, const px_key_range* range, int64_t max_groups, const px_batch* out,
+                         int32_t* d_out_seg, int64_t* d_ngroups, void* d_ws, size_t ws_bytes, void* stream) {
     set_error("");
     px_status s = check_batch(in, "px_groupby_agg in");
     if (s != PX_OK) return s;
@@ -298,7 +731,7 @@ px_status px_groupby_agg(const px_batch* in, const int32_t* key_cols, int32_t nk
         return fail(PX_ERR_INVALID, "px_groupby_agg: out has %d columns, %d expected", out->ncols, nkeys + naggs);
     if (out->nrows < max_groups)
         return fail(PX_ERR_INVALID, "px_groupby_agg: out capacity %lld below max_groups", (long long)out->nrows);
-    Spec sp;
+    Spec sp = {};
     sp.nkeys = nkeys;
     sp.keybits = 0;
     for (int k = 0; k < nkeys; ++k) {
@@ -319,6 +752,7 @@ px_status px_groupby_agg(const px_batch* in, const int32_t* key_cols, int32_t nk
         return fail(PX_ERR_UNSUPPORTED, "px_groupby_agg: %d key bits + %d segment bits exceed 64", sp.keybits,
                     sp.segbits);
     sp.naggs = naggs;
+    sp.count_agg = -1;
     for (int a = 0; a < naggs; ++a) {
         const px_agg& ag = aggs[a];
         if (ag.op != PX_COUNT && ag.op != PX_SUM && ag.op != PX_SUM_MUL)
@@ -326,6 +760,7 @@ px_status px_groupby_agg(const px_batch* in, const int32_t* key_cols, int32_t nk
         sp.op[a] = ag.op;
         sp.a_w[a] = sp.b_w[a] = 8;
         sp.a_in[a] = sp.b_in[a] = nullptr;
+        if (ag.op == PX_COUNT && sp.count_agg < 0) sp.count_agg = a;
         if (ag.op != PX_COUNT) {
             if (ag.a < 0 || ag.a >= in->ncols) return fail(PX_ERR_INVALID, "px_groupby_agg: aggregate %d column a", a);
             sp.a_w[a] = in->cols[ag.a].type;
@@ -343,31 +778,104 @@ px_status px_groupby_agg(const px_batch* in, const int32_t* key_cols, int32_t nk
     s = check_ws(d_ws, ws_bytes, px_groupby_ws_bytes(in->nrows, max_groups), "px_groupby_agg");
     if (s != PX_OK) return s;
 
+    // Dense block arrays when the key statistic makes the key space small enough.
+    size_t smem = 0;
+    sp.dense = 0;
+    sp.reps = 1;
+    sp.span[0] = sp.span[1] = 1;
+    if (range) {
+        bool ok = true;
+        uint64_t D = 1;
+        for (int k = 0; k < nkeys && ok; ++k) {
+            if (range->hi[k] < range->lo[k]) {
+                ok = false;
+                break;
+            }
+            const uint64_t span = static_cast<uint64_t>(range->hi[k]) - static_cast<uint64_t>(range->lo[k]) + 1;
+            if (span == 0 || span > (1ull << 24)) ok = false;
+            sp.lo[k] = range->lo[k];
+            sp.span[k] = span;
+            D *= span;
+        }
+        if (ok && D <= (1ull << 24)) {
+            sp.n64 = sp.n32 = 0;
+            for (int a = 0; a < naggs; ++a) {
+                sp.kind[a] = sp.op[a] == PX_COUNT ? 1 : 0;
+                sp.slot[a] = sp.kind[a] ? sp.n32++ : sp.n64++;
+            }
+            size_t per_rep = static_cast<size_t>(sp.n64) * D * 8 + static_cast<size_t>(sp.n32) * D * 4 +
+                             (sp.count_agg < 0 ? (D + 31) / 32 * 4 : 0);
+            per_rep = align_up(per_rep, 8);
+            if (per_rep > 0 && per_rep <= kSmemBudget) {
+                sp.dense = 1;
+                sp.D = static_cast<uint32_t>(D);
+                // One replica per thread when they fit (plain adds, no contention),
+                // with an odd number of 8-byte words per replica to spread the banks;
+                // else up to one per warp.
+                const size_t priv = (per_rep / 8) % 2 == 0 ? per_rep + 8 : per_rep;
+                if (priv * kThreads <= kSmemBudget) {
+                    sp.reps = kThreads;
+                    sp.rep_bytes = static_cast<uint32_t>(priv);
+                } else {
+                    while (sp.reps * 2 <= kWarps && per_rep * sp.reps * 2 <= kSmemBudget) sp.reps *= 2;
+                    sp.rep_bytes = static_cast<uint32_t>(per_rep);
+                }
+                smem = static_cast<size_t>(sp.rep_bytes) * sp.reps;
+            }
+        }
+    }
+    const uint32_t hslots = hash_slots(naggs);
+    if (!sp.dense) smem = static_cast<size_t>(hslots) * (12 + 8 * static_cast<size_t>(naggs));
+
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const uint32_t G = gtable_slots(max_groups);
-    char* base = static_cast<char*>(d_ws) + kWsScratch;
+    const WsLayout L = ws_layout(max_groups);
+    char* ws = static_cast<char*>(d_ws);
     GTable g;
-    g.ngroups = reinterpret_cast<unsigned long long*>(base);
-    g.state = reinterpret_cast<uint32_t*>(base + 256);
-    g.key = reinterpret_cast<unsigned long long*>(base + 256 + align_up(4ull * G, 256));
-    g.gidx = reinterpret_cast<int32_t*>(base + 256 + align_up(4ull * G, 256) + align_up(8ull * G, 256));
+    g.ngroups = reinterpret_cast<unsigned long long*>(ws + L.counter);
+    g.state = reinterpret_cast<uint32_t*>(ws + L.state);
+    g.key = reinterpret_cast<unsigned long long*>(ws + L.key);
+    g.gidx = reinterpret_cast<int32_t*>(ws + L.gidx);
     g.mask = G - 1;
-    cudaMemsetAsync(base, 0, 256 + 4ull * G, st);
+    cudaMemsetAsync(ws + L.counter, 0, 256 + 4ull * G, st);
     for (int a = 0; a < naggs; ++a) cudaMemsetAsync(sp.agg_out[a], 0, 8ull * max_groups, st);
+    // Dense global result when the whole (segment, key) space fits max_groups.
+    sp.dglobal = 0;
+    if (sp.dense) {
+        const uint64_t E = static_cast<uint64_t>(nsegs > 0 ? nsegs : 1) * sp.D;
+        if (E <= static_cast<uint64_t>(max_groups)) {
+            sp.dglobal = 1;
+            sp.E = E;
+            sp.dg_acc = reinterpret_cast<unsigned long long*>(ws + L.dg_acc);
+            sp.dg_occ = reinterpret_cast<uint32_t*>(ws + L.dg_occ);
+            cudaMemsetAsync(sp.dg_acc, 0, 8ull * naggs * E, st);
+            if (sp.count_agg < 0) cudaMemsetAsync(sp.dg_occ, 0, (E + 31) / 32 * 4, st);
+        }
+    }
     const int64_t ncap = in->nrows;
+    int32_t* status = &static_cast<WsHeader*>(d_ws)->status;
     if (ncap > 0) {
-        const uint32_t sslots = smem_slots(naggs);
-        const size_t smem = static_cast<size_t>(sslots) * (12 + 8 * static_cast<size_t>(naggs));
-        cudaFuncSetAttribute(groupby_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
-        int per_sm = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, groupby_kernel, kThreads, smem);
-        const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(cdiv(ncap, kTile),
-                                                                    static_cast<int64_t>(num_sms()) * std::max(1, per_sm)));
         const int64_t* d_n = d_sel ? d_nsel : in->d_nrows;
-        groupby_kernel<<<static_cast<unsigned>(grid), kThreads, smem, st>>>(
-            sp, d_sel, d_n, ncap, d_seg, g, max_groups, d_out_seg, &static_cast<WsHeader*>(d_ws)->status, sslots);
+        switch (naggs) {
+            case 0: s = launch<0>(sp, smem, d_sel, d_n, ncap, d_seg, g, max_groups, d_out_seg, status, hslots, st); break;
+            case 1: s = launch<1>(sp, smem, d_sel, d_n, ncap, d_seg, g, max_groups, d_out_seg, status, hslots, st); break;
+            case 2: s = launch<2>(sp, smem, d_sel, d_n, ncap, d_seg, g, max_groups, d_out_seg, status, hslots, st); break;
+            case 3: s = launch<3>(sp, smem, d_sel, d_n, ncap, d_seg, g, max_groups, d_out_seg, status, hslots, st); break;
+            case 4: s = launch<4>(sp, smem, d_sel, d_n, ncap, d_seg, g, max_groups, d_out_seg, status, hslots, st); break;
+            default:
+                s = launch<PX_MAX_AGGS>(sp, smem, d_sel, d_n, ncap, d_seg, g, max_groups, d_out_seg, status, hslots,
+                                        st);
+                break;
+        }
+        if (s != PX_OK) return s;
+    }
+    if (sp.dglobal) {
+        const int64_t ntiles = cdiv(static_cast<int64_t>(sp.E), kEmitTile);
+        cudaMemsetAsync(ws + L.emit_scan, 0, scan_scratch_bytes(ntiles), st);
+        dense_emit_kernel<<<static_cast<unsigned>(ntiles), kEmitThreads, 0, st>>>(
+            sp, g.ngroups, max_groups, d_out_seg, d_ngroups, scan_scratch(ws + L.emit_scan), status, ntiles);
         note_launch();
-        if ((s = check_launch("px_groupby_agg")) != PX_OK) return s;
+        return check_launch("px_groupby_agg emit");
     }
     cudaMemcpyAsync(d_ngroups, g.ngroups, sizeof(int64_t), cudaMemcpyDeviceToDevice, st);
     return check_launch("px_groupby_agg count");

@@ -115,11 +115,24 @@ __global__ void build_insert_kernel(TableView t, int32_t S, int32_t unique, cons
 }
 
 // ------------------------------------------------------------------ probe ----
+//
+// Three streaming launches, none of which waits on another block:
+//   match - per position, find the key's build row in its segment's table and
+//           record it (mrow: build row, -1 for no match, or -(slot + 2) for the
+//           first of several matches in a multi-map); per-tile match counts.
+//   scan  - exclusive scan of the tile counts: each tile's first output row.
+//   emit  - per tile, a block scan of the per-position match counts gives every
+//           output row; carried probe columns and gathered payload columns are
+//           written column by column, every load of a column before its stores.
+// The extra 4 bytes written and read per position buy the removal of the
+// serialised look-back that stalled a single-pass probe behind two dependent
+// memory round trips (key, then table slot) per tile.
 
 constexpr int kThreads = 256;
-constexpr int kItems = 8;
-constexpr int kTile = kThreads * kItems;
+constexpr int kItems = 4;
+constexpr int kTile = kThreads * kItems;  // 1024 positions
 constexpr int kWarps = kThreads / 32;
+constexpr int32_t kNoMatch = -1;
 
 struct OutCols {
     int32_t ncarry, npay;
@@ -137,6 +150,26 @@ __device__ __forceinline__ void copy_cell(void* out, const void* in, int w, int6
     else static_cast<int8_t*>(out)[dst] = static_cast<const int8_t*>(in)[src];
 }
 
+template <typename T>
+__device__ __forceinline__ void gather_store_t(const void* in, void* out, const int32_t* src, const int64_t* dst,
+                                               const bool* ok) {
+    T v[kItems];
+#pragma unroll
+    for (int i = 0; i < kItems; ++i)
+        if (ok[i]) v[i] = static_cast<const T*>(in)[src[i]];
+#pragma unroll
+    for (int i = 0; i < kItems; ++i)
+        if (ok[i]) static_cast<T*>(out)[dst[i]] = v[i];
+}
+
+// out[dst[i]] = in[src[i]] for the items with ok[i], all loads before the stores.
+__device__ __forceinline__ void gather_store(int w, const void* in, void* out, const int32_t* src, const int64_t* dst,
+                                             const bool* ok) {
+    if (w == 8) gather_store_t<int64_t>(in, out, src, dst, ok);
+    else if (w == 4) gather_store_t<int32_t>(in, out, src, dst, ok);
+    else gather_store_t<int8_t>(in, out, src, dst, ok);
+}
+
 __device__ __forceinline__ void emit(const OutCols& oc, int64_t pos, int64_t prow, int64_t brow,
                                      int32_t* probe_row, int32_t* build_row) {
     if (probe_row) probe_row[pos] = static_cast<int32_t>(prow);
@@ -145,68 +178,266 @@ __device__ __forceinline__ void emit(const OutCols& oc, int64_t pos, int64_t pro
     for (int c = 0; c < oc.npay; ++c) copy_cell(oc.pay_out[c], oc.pay_in[c], oc.pay_w[c], pos, brow);
 }
 
-__global__ void __launch_bounds__(kThreads)
-probe_kernel(TableView t, int32_t S, const int64_t* __restrict__ fk, const int32_t* __restrict__ sel,
-             const int64_t* __restrict__ d_n, int64_t ncap, const int64_t* __restrict__ pseg, OutCols oc,
-             int32_t* __restrict__ probe_row, int32_t* __restrict__ build_row, int64_t out_cap,
-             int64_t* __restrict__ d_nout, int64_t* __restrict__ d_out_seg, ScanScratch scan, int32_t* status,
-             int64_t ntiles, int64_t payload_rows) {
-    __shared__ int64_t s_tile;
-    __shared__ int64_t s_excl;
-    __shared__ int32_t s_warp[kWarps];
-    __shared__ int32_t s_bad;
-    const int64_t tile = next_tile(scan.counter, &s_tile);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (threadIdx.x == 0)
-        s_bad = (t.hdr->magic != kMagic || t.hdr->nsegs != S || (oc.npay > 0 && t.hdr->nbuild > payload_rows)) ? 1 : 0;
-    const int64_t n = actual_rows(d_n, ncap);
-    const bool unique = t.hdr->unique != 0;
-    const int64_t base = tile * kTile + warp * (32 * kItems);
-    __syncthreads();
-    const bool bad = s_bad != 0;
-    if (bad && threadIdx.x == 0) set_status(status, PX_ERR_INVALID);
+// Position of item i of this thread in a tile: warp-contiguous runs of 32 * kItems,
+// lanes innermost, so position order = (warp, item, lane).
+__device__ __forceinline__ int64_t tile_pos(int64_t tile, int warp, int i, int lane) {
+    return tile * kTile + warp * (32 * kItems) + i * 32 + lane;
+}
 
-    int32_t m[kItems];      // matches of this position
-    int32_t first[kItems];  // slot (within segment) of the first match
-    int32_t brow[kItems];   // build row of the first match
-    int32_t prow[kItems];
-    int32_t segq[kItems];
+// Segment of each valid position, advancing monotonically from q0 (the segment of
+// the tile's first position); positions of a thread increase with i.
+__device__ __forceinline__ void segments_of(const int64_t* pseg, int S, int q0, const int64_t* j, const bool* valid,
+                                            int* segq) {
+    int q = q0;
+    int64_t bound = (S > 1 && q + 1 < S) ? pseg[q + 1] : INT64_MAX;
 #pragma unroll
     for (int i = 0; i < kItems; ++i) {
-        const int64_t j = base + i * 32 + lane;
-        m[i] = 0;
-        first[i] = 0;
-        brow[i] = -1;
-        prow[i] = 0;
-        segq[i] = 0;
-        if (j < n && !bad) {
-            const int64_t r = sel ? static_cast<int64_t>(sel[j]) : j;
-            prow[i] = static_cast<int32_t>(r);
-            const int64_t key = fk[r];
-            const int q = S > 1 ? seg_of(pseg, S, j) : 0;
-            segq[i] = q;
-            if (key == kEmpty) continue;
-            const int64_t s0 = t.seg[q], s1 = t.seg[q + 1];
-            const Slot* seg_slots = t.slots + 2 * s0 + 2 * static_cast<int64_t>(q);
-            const uint32_t cap = static_cast<uint32_t>(2 * (s1 - s0) + 2);
-            uint32_t s = slot_of(fmix64(static_cast<uint64_t>(key)), cap);
-            for (uint32_t probe = 0; probe < cap; ++probe) {
-                const longlong2 v = *reinterpret_cast<const longlong2*>(&seg_slots[s]);
-                if (v.x == key) {
-                    if (m[i] == 0) {
-                        first[i] = static_cast<int32_t>(s);
-                        brow[i] = static_cast<int32_t>(v.y);
+        segq[i] = q;
+        if (!valid[i]) continue;
+        while (j[i] >= bound) {
+            ++q;
+            bound = q + 1 < S ? pseg[q + 1] : INT64_MAX;
+        }
+        segq[i] = q;
+    }
+}
+
+// Number of matches of `key` along the probe sequence from `s` in one segment's
+// slots, and the slot of the first one.
+__device__ __forceinline__ int32_t count_matches(const Slot* seg_slots, uint32_t cap, uint32_t s, int64_t key,
+                                                 uint32_t* first) {
+    int32_t m = 0;
+    for (uint32_t probe = 0; probe < cap; ++probe) {
+        const longlong2 v = *reinterpret_cast<const longlong2*>(&seg_slots[s]);
+        if (v.x == key) {
+            if (m == 0) *first = s;
+            ++m;
+        } else if (v.x == kEmpty) {
+            break;
+        }
+        if (++s == cap) s = 0;
+    }
+    return m;
+}
+
+__global__ void __launch_bounds__(kThreads)
+probe_match_kernel(TableView t, int32_t S, const int64_t* __restrict__ fk, const int32_t* __restrict__ sel,
+                   const int64_t* __restrict__ d_n, int64_t ncap, const int64_t* __restrict__ pseg,
+                   int32_t* __restrict__ mrow, int32_t* __restrict__ tile_cnt, int32_t* status, int32_t npay,
+                   int64_t payload_rows) {
+    __shared__ int32_t s_bad, s_q0, s_unique;
+    __shared__ int32_t s_warp[kWarps];
+    const int64_t tile = blockIdx.x;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t n = actual_rows(d_n, ncap);
+    if (threadIdx.x == 0) {
+        s_bad = (t.hdr->magic != kMagic || t.hdr->nsegs != S || (npay > 0 && t.hdr->nbuild > payload_rows)) ? 1 : 0;
+        if (s_bad && tile == 0) set_status(status, PX_ERR_INVALID);
+        s_unique = t.hdr->unique;
+        const int64_t p0 = tile * kTile;
+        s_q0 = (S > 1 && p0 < n) ? seg_of(pseg, S, p0) : 0;
+    }
+    __syncthreads();
+    const bool bad = s_bad != 0, unique = s_unique != 0;
+    int64_t j[kItems], keyv[kItems];
+    int32_t prow[kItems], out[kItems];
+    bool valid[kItems];
+#pragma unroll
+    for (int i = 0; i < kItems; ++i) {
+        j[i] = tile_pos(tile, warp, i, lane);
+        valid[i] = j[i] < n && !bad;
+        prow[i] = valid[i] ? (sel ? sel[j[i]] : static_cast<int32_t>(j[i])) : 0;
+        out[i] = kNoMatch;
+    }
+#pragma unroll
+    for (int i = 0; i < kItems; ++i) keyv[i] = valid[i] ? fk[prow[i]] : kEmpty;
+    int segq[kItems];
+    segments_of(pseg, S, s_q0, j, valid, segq);
+    int64_t sbase[kItems];
+    uint32_t scap[kItems], shome[kItems];
+    {
+        int tq = -1;
+        int64_t t0 = 0, t1 = 0;
+#pragma unroll
+        for (int i = 0; i < kItems; ++i) {
+            sbase[i] = 0;
+            scap[i] = 1;
+            shome[i] = 0;
+            if (!valid[i] || keyv[i] == kEmpty) continue;
+            if (segq[i] != tq) {
+                tq = segq[i];
+                t0 = t.seg[tq];
+                t1 = t.seg[tq + 1];
+            }
+            sbase[i] = 2 * t0 + 2 * static_cast<int64_t>(tq);
+            scap[i] = static_cast<uint32_t>(2 * (t1 - t0) + 2);
+            shome[i] = slot_of(fmix64(static_cast<uint64_t>(keyv[i])), scap[i]);
+        }
+    }
+    int32_t cnt = 0;
+    if (unique) {
+        // The home slot and the next one for every item first (load factor <= 1/2
+        // settles most probes there), then continue only where both hold other keys.
+        longlong2 v0[kItems], v1[kItems];
+#pragma unroll
+        for (int i = 0; i < kItems; ++i) {
+            if (valid[i] && keyv[i] != kEmpty) {
+                const uint32_t s1 = shome[i] + 1 == scap[i] ? 0 : shome[i] + 1;
+                v0[i] = *reinterpret_cast<const longlong2*>(&t.slots[sbase[i] + shome[i]]);
+                v1[i] = *reinterpret_cast<const longlong2*>(&t.slots[sbase[i] + s1]);
+            } else {
+                v0[i] = make_longlong2(kEmpty, 0);
+                v1[i] = v0[i];
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < kItems; ++i) {
+            if (!valid[i] || keyv[i] == kEmpty) continue;
+            const int64_t key = keyv[i];
+            if (v0[i].x == key) {
+                out[i] = static_cast<int32_t>(v0[i].y);
+            } else if (v0[i].x != kEmpty) {
+                if (v1[i].x == key) {
+                    out[i] = static_cast<int32_t>(v1[i].y);
+                } else if (v1[i].x != kEmpty) {
+                    const Slot* seg_slots = t.slots + sbase[i];
+                    uint32_t s = shome[i] + 2;
+                    if (s >= scap[i]) s -= scap[i];
+                    for (uint32_t probe = 2; probe < scap[i]; ++probe) {
+                        const longlong2 v = *reinterpret_cast<const longlong2*>(&seg_slots[s]);
+                        if (v.x == key) {
+                            out[i] = static_cast<int32_t>(v.y);
+                            break;
+                        }
+                        if (v.x == kEmpty) break;
+                        if (++s == scap[i]) s = 0;
                     }
-                    ++m[i];
-                    if (unique) break;
-                } else if (v.x == kEmpty) {
-                    break;
                 }
-                if (++s == cap) s = 0;
+            }
+            cnt += out[i] != kNoMatch ? 1 : 0;
+        }
+    } else {
+        // Multi-map: count every match; one match is recorded as its build row,
+        // several as -(global slot of the first + 2) for the emit pass to walk.
+#pragma unroll
+        for (int i = 0; i < kItems; ++i) {
+            if (!valid[i] || keyv[i] == kEmpty) continue;
+            uint32_t first = 0;
+            const Slot* seg_slots = t.slots + sbase[i];
+            const int32_t m = count_matches(seg_slots, scap[i], shome[i], keyv[i], &first);
+            if (m == 1) out[i] = seg_slots[first].row;
+            else if (m > 1) out[i] = -static_cast<int32_t>(sbase[i] + first) - 2;
+            cnt += m;
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < kItems; ++i)
+        if (j[i] < ncap) mrow[j[i]] = out[i];
+    cnt = warp_sum(cnt);
+    if (lane == 0) s_warp[warp] = cnt;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int32_t total = 0;
+        for (int w = 0; w < kWarps; ++w) total += s_warp[w];
+        tile_cnt[tile] = total;
+    }
+}
+
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 8;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+// Exclusive scan of the tile counts (single pass, bounded look-back); the last
+// tile writes the total to *d_nout and flags an output over capacity.
+__global__ void __launch_bounds__(kScanThreads)
+probe_scan_kernel(const int32_t* __restrict__ cnt, int64_t* __restrict__ off, int64_t total, int64_t out_cap,
+                  int64_t* __restrict__ d_nout, ScanScratch scan, int32_t* status, int64_t nscan_tiles) {
+    __shared__ int64_t s_tile;
+    __shared__ int64_t s_warp[kScanThreads / 32];
+    __shared__ int64_t s_excl;
+    const int64_t tile = next_tile(scan.counter, &s_tile);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t base = tile * kScanTile + static_cast<int64_t>(tid) * kScanItems;
+    int64_t v[kScanItems];
+    int64_t sum = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        v[k] = base + k < total ? cnt[base + k] : 0;
+        sum += v[k];
+    }
+    const int64_t incl = warp_incl_scan(sum);
+    if (lane == 31) s_warp[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        const int64_t w = lane < kScanThreads / 32 ? s_warp[lane] : 0;
+        const int64_t wi = warp_incl_scan(w);
+        if (lane < kScanThreads / 32) s_warp[lane] = wi - w;
+        const int64_t agg = __shfl_sync(FULL, wi, 31);
+        const int64_t excl = lookback(scan.states, tile, agg, status);
+        if (lane == 0) {
+            s_excl = excl;
+            if (tile == nscan_tiles - 1) {
+                *d_nout = excl + agg;
+                if (excl + agg > out_cap) set_status(status, PX_ERR_CAPACITY);
             }
         }
     }
-    // Exclusive output offsets in position order (warp, item, lane).
+    __syncthreads();
+    int64_t run = s_excl + s_warp[warp] + incl - sum;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        if (base + k < total) off[base + k] = run;
+        run += v[k];
+    }
+}
+__global__ void __launch_bounds__(kThreads)
+probe_emit_kernel(TableView t, int32_t S, const int64_t* __restrict__ fk, const int32_t* __restrict__ sel,
+                  const int64_t* __restrict__ d_n, int64_t ncap, const int64_t* __restrict__ pseg,
+                  const int32_t* __restrict__ mrow, const int64_t* __restrict__ tile_off, OutCols oc,
+                  int32_t* __restrict__ probe_row, int32_t* __restrict__ build_row, int64_t out_cap,
+                  int64_t* __restrict__ d_out_seg) {
+    __shared__ int32_t s_q0;
+    __shared__ int32_t s_warp[kWarps];
+    const int64_t tile = blockIdx.x;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t n = actual_rows(d_n, ncap);
+    int64_t j[kItems];
+    int32_t mr[kItems], prow[kItems], m[kItems];
+    bool valid[kItems];
+#pragma unroll
+    for (int i = 0; i < kItems; ++i) {
+        j[i] = tile_pos(tile, warp, i, lane);
+        valid[i] = j[i] < n;
+        mr[i] = valid[i] ? mrow[j[i]] : kNoMatch;
+        prow[i] = valid[i] ? (sel ? sel[j[i]] : static_cast<int32_t>(j[i])) : 0;
+    }
+    // Matches per position: 1, 0, or (multi-map, -1 here) counted again below.
+#pragma unroll
+    for (int i = 0; i < kItems; ++i) m[i] = mr[i] >= 0 ? 1 : (mr[i] == kNoMatch ? 0 : -1);
+    if (threadIdx.x == 0) {
+        const int64_t p0 = tile * kTile;
+        s_q0 = (S > 1 && p0 < n) ? seg_of(pseg, S, p0) : 0;
+    }
+    __syncthreads();
+    int segq[kItems];
+    segments_of(pseg, S, s_q0, j, valid, segq);
+    int64_t key[kItems];
+#pragma unroll
+    for (int i = 0; i < kItems; ++i) {
+        key[i] = 0;
+        if (m[i] >= 0) continue;
+        // Multi-map: count the matches along the probe chain from the first one.
+        const int q = segq[i];
+        const int64_t t0 = t.seg[q], t1 = t.seg[q + 1];
+        const int64_t sb = 2 * t0 + 2 * static_cast<int64_t>(q);
+        const uint32_t cap = static_cast<uint32_t>(2 * (t1 - t0) + 2);
+        const uint32_t first = static_cast<uint32_t>(-static_cast<int64_t>(mr[i]) - 2 - sb);
+        key[i] = fk[prow[i]];
+        uint32_t dummy = 0;
+        m[i] = count_matches(t.slots + sb, cap, first, key[i], &dummy);
+    }
+    // Output rows in position order (warp, item, lane): warp scans, then a block
+    // combine; the tile's first row comes from the scan of the tile counts.
     int32_t pre[kItems];
     int32_t wsum = 0;
 #pragma unroll
@@ -217,47 +448,46 @@ probe_kernel(TableView t, int32_t S, const int64_t* __restrict__ fk, const int32
     }
     if (lane == 0) s_warp[warp] = wsum;
     __syncthreads();
-    if (warp == 0) {
-        const int32_t w = lane < kWarps ? s_warp[lane] : 0;
-        const int32_t incl = warp_incl_scan(w);
-        const int32_t total = __shfl_sync(FULL, incl, 31);
-        if (lane < kWarps) s_warp[lane] = incl - w;
-        const int64_t excl = lookback(scan.states, tile, total, status);
-        if (lane == 0) {
-            s_excl = excl;
-            if (tile == ntiles - 1) {
-                *d_nout = excl + total;
-                if (excl + total > out_cap) set_status(status, PX_ERR_CAPACITY);
-            }
-        }
-    }
-    __syncthreads();
-    const int64_t wbase = s_excl + s_warp[warp];
+    int32_t wbase = 0;
+    for (int w = 0; w < warp; ++w) wbase += s_warp[w];
+    const int64_t base = tile_off[tile] + wbase;
+    int64_t pos[kItems];
+    bool one[kItems];
 #pragma unroll
     for (int i = 0; i < kItems; ++i) {
-        const int64_t j = base + i * 32 + lane;
-        const int64_t pos0 = wbase + pre[i];
-        if (d_out_seg && j < n) {
-            for (int q = segq[i]; q >= 0 && (S > 1 ? pseg[q] == j : j == 0); --q) d_out_seg[q] = pos0;
+        pos[i] = base + pre[i];
+        one[i] = mr[i] >= 0 && pos[i] < out_cap;
+        if (d_out_seg && valid[i]) {
+            for (int q = segq[i]; q >= 0 && (S > 1 ? pseg[q] == j[i] : j[i] == 0); --q) d_out_seg[q] = pos[i];
         }
-        if (m[i] == 0) continue;
-        if (unique || m[i] == 1) {
-            if (pos0 < out_cap) emit(oc, pos0, prow[i], brow[i], probe_row, build_row);
-            continue;
-        }
-        // Multi-match: walk the probe sequence again from the first match.
+    }
+    if (probe_row) {
+#pragma unroll
+        for (int i = 0; i < kItems; ++i)
+            if (one[i]) probe_row[pos[i]] = prow[i];
+    }
+    if (build_row) {
+#pragma unroll
+        for (int i = 0; i < kItems; ++i)
+            if (one[i]) build_row[pos[i]] = mr[i];
+    }
+    for (int c = 0; c < oc.ncarry; ++c) gather_store(oc.carry_w[c], oc.carry_in[c], oc.carry_out[c], prow, pos, one);
+    for (int c = 0; c < oc.npay; ++c) gather_store(oc.pay_w[c], oc.pay_in[c], oc.pay_out[c], mr, pos, one);
+    // Positions with several matches: walk the chain again, emitting each.
+#pragma unroll
+    for (int i = 0; i < kItems; ++i) {
+        if (mr[i] >= kNoMatch) continue;
         const int q = segq[i];
-        const int64_t s0 = t.seg[q], s1 = t.seg[q + 1];
-        const Slot* seg_slots = t.slots + 2 * s0 + 2 * static_cast<int64_t>(q);
-        const uint32_t cap = static_cast<uint32_t>(2 * (s1 - s0) + 2);
-        const int64_t key = fk[prow[i]];
-        uint32_t s = static_cast<uint32_t>(first[i]);
-        int64_t pos = pos0;
-        for (uint32_t probe = 0; probe < cap && pos < pos0 + m[i]; ++probe) {
-            const longlong2 v = *reinterpret_cast<const longlong2*>(&seg_slots[s]);
-            if (v.x == key) {
-                if (pos < out_cap) emit(oc, pos, prow[i], static_cast<int32_t>(v.y), probe_row, build_row);
-                ++pos;
+        const int64_t t0 = t.seg[q], t1 = t.seg[q + 1];
+        const int64_t sb = 2 * t0 + 2 * static_cast<int64_t>(q);
+        const uint32_t cap = static_cast<uint32_t>(2 * (t1 - t0) + 2);
+        uint32_t s = static_cast<uint32_t>(-static_cast<int64_t>(mr[i]) - 2 - sb);
+        int64_t p = pos[i];
+        for (uint32_t probe = 0; probe < cap && p < pos[i] + m[i]; ++probe) {
+            const longlong2 v = *reinterpret_cast<const longlong2*>(&t.slots[sb + s]);
+            if (v.x == key[i]) {
+                if (p < out_cap) emit(oc, p, prow[i], static_cast<int32_t>(v.y), probe_row, build_row);
+                ++p;
             } else if (v.x == kEmpty) {
                 break;
             }
@@ -275,6 +505,26 @@ __global__ void probe_seg_tail_kernel(const int64_t* __restrict__ pseg, int32_t 
         const int64_t start = segmented ? pseg[q] : (q == 0 ? 0 : n);
         if (start >= n) d_out_seg[q] = *d_nout;
     }
+}
+
+// Probe workspace: [header][mrow: 4 B per position][tile counts][tile offsets]
+// [scan scratch over the tile counts].
+struct ProbeWs {
+    size_t mrow, cnt, off, scan, total;
+    int64_t ntiles, nscan;
+};
+
+ProbeWs probe_ws_layout(int64_t nprobe) {
+    if (nprobe < 0) nprobe = 0;
+    ProbeWs L;
+    L.ntiles = cdiv(nprobe, kTile);
+    L.nscan = cdiv(L.ntiles, kScanTile);
+    L.mrow = kWsScratch;
+    L.cnt = L.mrow + align_up(4 * static_cast<size_t>(nprobe), 256);
+    L.off = L.cnt + align_up(4 * static_cast<size_t>(L.ntiles), 256);
+    L.scan = L.off + align_up(8 * static_cast<size_t>(L.ntiles), 256);
+    L.total = L.scan + scan_scratch_bytes(L.nscan);
+    return L;
 }
 
 }  // namespace
@@ -296,8 +546,7 @@ size_t px_join_build_ws_bytes(int64_t nbuild) {
 }
 
 size_t px_join_probe_ws_bytes(int64_t nprobe) {
-    if (nprobe < 0) nprobe = 0;
-    return kWsScratch + scan_scratch_bytes(cdiv(nprobe, kTile));
+    return probe_ws_layout(nprobe).total;
 }
 
 px_status px_join_build(const px_batch* build, int32_t pk_col, const int64_t* d_seg, int32_t nsegs, int32_t unique,
@@ -315,6 +564,8 @@ px_status px_join_build(const px_batch* build, int32_t pk_col, const int64_t* d_
     if (table_bytes < px_join_table_bytes(build->nrows, nsegs))
         return fail(PX_ERR_INVALID, "px_join_build: table of %zu bytes, %zu needed", table_bytes,
                     px_join_table_bytes(build->nrows, nsegs));
+    if (!unique && build->nrows >= (int64_t(1) << 30))
+        return fail(PX_ERR_UNSUPPORTED, "px_join_build: multi-map tables hold below 2^30 rows");
     s = check_ws(d_ws, ws_bytes, px_join_build_ws_bytes(build->nrows), "px_join_build");
     if (s != PX_OK) return s;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -397,15 +648,27 @@ px_status px_join_probe(const void* d_table, const px_batch* probe, int32_t fk_c
         if (d_out_seg) cudaMemsetAsync(d_out_seg, 0, sizeof(int64_t) * (S + 1), st);
         return check_launch("px_join_probe");
     }
-    const int64_t ntiles = cdiv(ncap, kTile);
-    char* scratch = static_cast<char*>(d_ws) + kWsScratch;
-    cudaMemsetAsync(scratch, 0, scan_scratch_bytes(ntiles), st);
-    probe_kernel<<<static_cast<unsigned>(ntiles), kThreads, 0, st>>>(
-        t, S, static_cast<const int64_t*>(probe->cols[fk_col].data), d_sel, d_n, ncap, d_seg, oc, d_probe_row,
-        d_build_row, out->nrows, d_nout, d_out_seg, scan_scratch(scratch), &static_cast<WsHeader*>(d_ws)->status,
-        ntiles, build_payload ? build_payload->nrows : 0);
+    const ProbeWs L = probe_ws_layout(ncap);
+    char* ws = static_cast<char*>(d_ws);
+    int32_t* mrow = reinterpret_cast<int32_t*>(ws + L.mrow);
+    int32_t* tcnt = reinterpret_cast<int32_t*>(ws + L.cnt);
+    int64_t* toff = reinterpret_cast<int64_t*>(ws + L.off);
+    int32_t* status = &static_cast<WsHeader*>(d_ws)->status;
+    const int64_t* fk = static_cast<const int64_t*>(probe->cols[fk_col].data);
+    const unsigned grid = static_cast<unsigned>(L.ntiles);
+    probe_match_kernel<<<grid, kThreads, 0, st>>>(t, S, fk, d_sel, d_n, ncap, d_seg, mrow, tcnt, status, npay,
+                                                  build_payload ? build_payload->nrows : 0);
     note_launch();
-    if ((s = check_launch("px_join_probe")) != PX_OK) return s;
+    if ((s = check_launch("px_join_probe match")) != PX_OK) return s;
+    cudaMemsetAsync(ws + L.scan, 0, scan_scratch_bytes(L.nscan), st);
+    probe_scan_kernel<<<static_cast<unsigned>(L.nscan), kScanThreads, 0, st>>>(
+        tcnt, toff, L.ntiles, out->nrows, d_nout, scan_scratch(ws + L.scan), status, L.nscan);
+    note_launch();
+    if ((s = check_launch("px_join_probe scan")) != PX_OK) return s;
+    probe_emit_kernel<<<grid, kThreads, 0, st>>>(t, S, fk, d_sel, d_n, ncap, d_seg, mrow, toff, oc, d_probe_row,
+                                                 d_build_row, out->nrows, d_out_seg);
+    note_launch();
+    if ((s = check_launch("px_join_probe emit")) != PX_OK) return s;
     if (d_out_seg) {
         probe_seg_tail_kernel<<<1, 256, 0, st>>>(d_seg, S, nsegs > 0 ? 1 : 0, d_n, ncap, d_nout, d_out_seg);
         note_launch();

@@ -29,10 +29,12 @@ class PlainPipeline:
 
     NAMES = ["key", "price", "qty", "date", "flag", "status"]
 
-    def __init__(self, d: dict, lo: int, hi: int, nparts: int = 8, seed: int = 0, max_groups: int = 256):
+    def __init__(self, d: dict, lo: int, hi: int, nparts: int = 8, seed: int = 0, max_groups: int = 256,
+                 key_range=((0, 3), (0, 1))):
         L = load()
         self.d = d
         self.lo, self.hi, self.nparts, self.seed, self.max_groups = lo, hi, nparts, seed, max_groups
+        self.key_range = key_range  # catalog statistic of (flag, status); speed only
         n = d["key"].numel()
         dev = d["key"].device
         self.cols = [d[k] for k in self.NAMES]
@@ -51,7 +53,8 @@ class PlainPipeline:
                      offsets=self.offsets, ws=self.ws, stream=stream)
         g = px_groupby_agg(self.parts, [4, 5], [(PX_SUM, 1, None), (PX_SUM_MUL, 1, 2), (PX_SUM, 2, None),
                                                 (PX_COUNT, None, None)],
-                           max_groups=self.max_groups, d_nrows=self.nsel, out=self.gout, ws=self.ws, stream=stream)
+                           max_groups=self.max_groups, d_nrows=self.nsel, key_range=self.key_range, out=self.gout,
+                           ws=self.ws, stream=stream)
         return {"sel": self.sel, "nsel": self.nsel, "parts": dict(zip(self.NAMES, self.parts)),
                 "offsets": self.offsets, "groups": g}
 
@@ -60,10 +63,11 @@ class JoinPipeline:
     """fact.date filter -> build on dim.pk -> probe fact.fk (carry amount, gather
     dim.attr) -> group by attr: SUM(amount), COUNT(*)."""
 
-    def __init__(self, d: dict, lo: int, hi: int, max_groups: int = 64):
+    def __init__(self, d: dict, lo: int, hi: int, max_groups: int = 64, attr_range=(0, 24)):
         L = load()
         self.d = d
         self.lo, self.hi, self.max_groups = lo, hi, max_groups
+        self.attr_range = attr_range  # catalog statistic of dim.attr; speed only
         nf, nd = d["fk"].numel(), d["pk"].numel()
         dev = d["fk"].device
         self.fact = [d["fk"], d["amount"], d["date"]]
@@ -85,7 +89,8 @@ class JoinPipeline:
         j = px_join_probe(self.table, self.fact, 0, sel=self.sel, nsel=self.nsel, carry=[1], payload=[self.d["attr"]],
                           out=self.jout, out_cap=self.jout[0].numel(), ws=self.ws, stream=stream)
         g = px_groupby_agg(self.jout, [1], [(PX_SUM, 0, None), (PX_COUNT, None, None)], max_groups=self.max_groups,
-                           d_nrows=j["nout"], out=self.gout, ws=self.ws, stream=stream)
+                           d_nrows=j["nout"], key_range=[self.attr_range] if self.attr_range else None,
+                           out=self.gout, ws=self.ws, stream=stream)
         return {"sel": self.sel, "nsel": self.nsel, "join": j, "groups": g}
 
 
@@ -93,10 +98,15 @@ class AtScalePipeline:
     """Exchange both sides on the join key into nparts partitions, join per partition,
     Partial group-by attr per partition (SUM(amount), COUNT(*)), Final merge by attr."""
 
-    def __init__(self, d: dict, nparts: int = 64, seed: int = 0, nattr_bound: int = 10_000):
+    CALLS = ["px_partition(dim)", "px_partition(fact)", "px_join_build", "px_join_probe",
+             "px_groupby_agg(partial)", "px_groupby_agg(final)"]
+
+    def __init__(self, d: dict, nparts: int = 64, seed: int = 0, nattr_bound: int = 10_000, attr_range="auto"):
         L = load()
         self.d = d
         self.nparts, self.seed = nparts, seed
+        # catalog statistic of dim.attr (speed only); "auto": the attribute's domain [0, nattr_bound)
+        self.attr_range = (0, nattr_bound - 1) if attr_range == "auto" else attr_range
         nf, nd = d["fk"].numel(), d["pk"].numel()
         dev = d["fk"].device
         self.fact = [d["fk"], d["amount"], d["date"]]
@@ -119,16 +129,27 @@ class AtScalePipeline:
                    L.px_groupby_ws_bytes(nf, self.max_partial))
         self.ws = Workspace(need)
 
-    def run(self, stream=None) -> dict:
+    def run(self, stream=None, mark=None) -> dict:
+        """One pass of the pipeline. mark(i), if given, is called before call i and
+        after the last one (i = 0..6), e.g. to record CUDA events between the calls."""
         P, ws = self.nparts, self.ws
+        rng = [self.attr_range] if self.attr_range else None
+        mark = mark or (lambda i: None)
+        mark(0)
         px_partition(self.dim, 0, P, self.seed, out=self.dparts, offsets=self.doff, ws=ws, stream=stream)
+        mark(1)
         px_partition(self.fact, 0, P, self.seed, out=self.fparts, offsets=self.foff, ws=ws, stream=stream)
+        mark(2)
         px_join_build(self.dparts, 0, seg=self.doff, unique=True, table=self.table, ws=ws, stream=stream)
+        mark(3)
         j = px_join_probe(self.table, self.fparts, 0, seg=self.foff, carry=[1], payload=[self.dparts[1]],
                           out=self.jout, out_cap=self.jout[0].numel(), out_seg=True, ws=ws, stream=stream)
+        mark(4)
         part = px_groupby_agg(self.jout, [1], [(PX_SUM, 0, None), (PX_COUNT, None, None)],
-                              max_groups=self.max_partial, seg=j["out_seg"], d_nrows=j["nout"], out=self.pout,
-                              ws=ws, stream=stream)
+                              max_groups=self.max_partial, seg=j["out_seg"], d_nrows=j["nout"], key_range=rng,
+                              out=self.pout, ws=ws, stream=stream)
+        mark(5)
         final = px_groupby_agg(self.pout, [0], [(PX_SUM, 1, None), (PX_SUM, 2, None)], max_groups=self.max_final,
-                               d_nrows=part["ngroups"], out=self.fout, ws=ws, stream=stream)
+                               d_nrows=part["ngroups"], key_range=rng, out=self.fout, ws=ws, stream=stream)
+        mark(6)
         return {"dim_offsets": self.doff, "fact_offsets": self.foff, "join": j, "partial": part, "final": final}

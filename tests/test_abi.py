@@ -115,10 +115,10 @@ def test_host_checks(lib):
     g_out = _batch(pxm, [pxm.PX_I64, pxm.PX_I64], 100)
     keys = (ctypes.c_int32 * 1)(0)
     aggs = (pxm.px_agg * 1)(pxm.px_agg(pxm.PX_SUM, 1, -1))
-    r = lib.px_groupby_agg(ctypes.byref(g_in), keys, 1, aggs, 1, None, None, FAKE, 4, 100, ctypes.byref(g_out),
-                           None, FAKE, ws, wsz, None)
+    r = lib.px_groupby_agg(ctypes.byref(g_in), keys, 1, aggs, 1, None, None, FAKE, 4, None, 100,
+                           ctypes.byref(g_out), None, FAKE, ws, wsz, None)
     assert r == pxm.PX_ERR_UNSUPPORTED and "bits" in pxm.last_error()
-    r = lib.px_groupby_agg(ctypes.byref(g_in), keys, 1, aggs, 1, None, None, None, 0, 100, ctypes.byref(inb),
+    r = lib.px_groupby_agg(ctypes.byref(g_in), keys, 1, aggs, 1, None, None, None, 0, None, 100, ctypes.byref(inb),
                            None, FAKE, ws, wsz, None)
     assert r == pxm.PX_ERR_INVALID
 

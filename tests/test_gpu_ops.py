@@ -229,8 +229,19 @@ def test_groupby_parity(px, kt):
                     (px.PX_SUM_MUL, nk, nk)]
             want = oracle.groupby(keys, [(oracle.SUM, a64, None), (oracle.COUNT, None, None),
                                          (oracle.SUM_MUL, a32, b8), (oracle.SUM_MUL, a64, a64)])
-            res = _gb(px, cols, list(range(nk)), aggs, max(1, want["ngroups"]))
-            assert_groups_equal(res, want, nk)
+            # hash path (no statistic), exact range, half range (dense + spill), wrong range
+            for rng in [None, "exact", "half", "wrong"]:
+                kr = None
+                if rng is not None and n:
+                    lo = [int(k.min()) for k in keys]
+                    hi = [int(k.max()) for k in keys]
+                    if rng == "half":
+                        hi = [l + (h - l) // 2 for l, h in zip(lo, hi)]
+                    elif rng == "wrong":
+                        lo, hi = [h + 1 for h in hi], [h + 5 for h in hi]
+                    kr = list(zip(lo, hi))
+                res = _gb(px, cols, list(range(nk)), aggs, max(1, want["ngroups"]), key_range=kr)
+                assert_groups_equal(res, want, nk)
 
 
 def test_groupby_selection_and_device_count(px):
@@ -279,6 +290,46 @@ def test_groupby_many_groups_spill_to_global(px):
     want = oracle.groupby([k], [(oracle.SUM, a, None), (oracle.COUNT, None, None)])
     res = _gb(px, [k, a], [0], [(px.PX_SUM, 1, None), (px.PX_COUNT, None, None)], want["ngroups"])
     assert_groups_equal(res, want, 1)
+
+
+@pytest.mark.parametrize("dense", [False, True])
+def test_groupby_without_count_distinct_and_many_aggs(px, dense):
+    g = pxdata.rng(404)
+    n = 150_001
+    k0 = pxdata.random_column(g, n, np.int32, -20, 20)
+    k1 = pxdata.random_column(g, n, np.int8, 0, 3)
+    a = pxdata.random_column(g, n, np.int64, -10**12, 10**12)
+    b = pxdata.random_column(g, n, np.int32)
+    kr = [(-20, 20), (0, 3)] if dense else None
+    cols = [k0, k1, a, b]
+    # no COUNT: occupancy comes from a bitmap in dense mode
+    want = oracle.groupby([k0, k1], [(oracle.SUM, a, None), (oracle.SUM_MUL, a, b)])
+    res = _gb(px, cols, [0, 1], [(px.PX_SUM, 2, None), (px.PX_SUM_MUL, 2, 3)], want["ngroups"], key_range=kr)
+    assert_groups_equal(res, want, 2)
+    # DISTINCT: no aggregates at all
+    want = oracle.groupby([k0, k1], [])
+    res = _gb(px, cols, [0, 1], [], want["ngroups"], key_range=kr)
+    assert_groups_equal(res, want, 2)
+    # more than four aggregates (the generic kernel)
+    ops = [(oracle.SUM, a, None), (oracle.COUNT, None, None), (oracle.SUM, b, None), (oracle.SUM_MUL, a, b),
+           (oracle.SUM_MUL, b, b), (oracle.SUM, k0, None)]
+    gops = [(px.PX_SUM, 2, None), (px.PX_COUNT, None, None), (px.PX_SUM, 3, None), (px.PX_SUM_MUL, 2, 3),
+            (px.PX_SUM_MUL, 3, 3), (px.PX_SUM, 0, None)]
+    want = oracle.groupby([k0, k1], ops)
+    res = _gb(px, cols, [0, 1], gops, want["ngroups"], key_range=kr)
+    assert_groups_equal(res, want, 2)
+
+
+def test_groupby_dense_segmented_hot_partition(px):
+    # Partial mode over Zipf-skewed segments with the dense path (the at-scale shape).
+    d = pxdata.plain_at_scale(20_000, 400_000, nattr=500)
+    pr, br, _ = oracle.join(d["pk"], d["fk"])
+    attr, amount = d["attr"][br], d["amount"][pr]
+    seg = np.array([0, 1000, 1000, 250_000, 399_999, 400_000], np.int64)
+    want = oracle.groupby([attr], [(oracle.SUM, amount, None), (oracle.COUNT, None, None)], seg=seg)
+    res = _gb(px, [attr, amount], [0], [(px.PX_SUM, 1, None), (px.PX_COUNT, None, None)], want["ngroups"],
+              seg=dev(seg), key_range=[(0, 499)])
+    assert_groups_equal(res, want, 1, segmented=True)
 
 
 def test_groupby_capacity_overflow_reported(px):
