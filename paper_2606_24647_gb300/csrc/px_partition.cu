@@ -3,26 +3,31 @@
 // 0's rows, then partition 1's, ... (stable), plus offsets[nparts+1]: the
 // UcxExchange's "size metadata, then packed GPU data" for every destination.
 //
-// Three launches over tiles of 4096 positions:
-//   1. hist    - per-tile partition counts, stored partition-major: cnt[q][t].
+// Three launches over tiles of T positions (T = 512, 1024 or 2048, chosen so a
+// tile of every column fits the shared-memory staging area):
+//   1. hist    - per-tile partition counts, stored partition-major: cnt[q][t]
+//                (per-warp shared counters, native 32-bit atomics).
 //   2. scan    - exclusive scan of cnt in that order gives each (partition, tile)
 //                its global output start (single pass, bounded look-back), and
 //                offsets[q] = start of (q, tile 0).
-//   3. scatter - recomputes each row's partition, ranks rows stably inside the
-//                tile (warp match_any + per-warp counters, rows in order), then
-//                for each column stages the tile in shared memory grouped by
-//                partition and writes each partition's run contiguously, so the
-//                stores coalesce. The key column is read twice (hist and
-//                scatter); every other column once; every column written once.
+//   3. scatter - stages the tile of every column into shared memory with one TMA
+//                bulk copy per column (all in flight together, completed on an
+//                mbarrier; plain loads for gathers through a selection and for a
+//                ragged last tile), ranks rows stably inside the tile with a warp
+//                multi-split (one ballot per partition-id bit gives the lanes with
+//                the same partition) and per-warp counters, then per column moves
+//                the values into partition order in shared memory and writes each
+//                partition's run contiguously, so the stores coalesce.
+// The key column is read twice (hist and scatter); every other column once; every
+// column written once.
 #include "px_common.cuh"
 
 namespace px {
 namespace {
 
-constexpr int kThreads = 512;
-constexpr int kItems = 8;
-constexpr int kTile = kThreads * kItems;  // 4096 positions
+constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
+constexpr size_t kStageBudget = 48 * 1024;  // raw tile staging bytes (all columns)
 
 constexpr int kScanThreads = 256;
 constexpr int kScanItems = 8;
@@ -33,39 +38,52 @@ struct Cols {
     int32_t width[PX_MAX_COLS];
     const void* in[PX_MAX_COLS];
     void* out[PX_MAX_COLS];
+    uint32_t stage_off[PX_MAX_COLS];  // byte offset of the column's tile in the staging area
 };
 
-// Local position of item i of this thread inside a tile: warp-contiguous runs of
-// 32 * kItems positions, lanes innermost, so position order = (warp, item, lane).
-__device__ __forceinline__ int local_pos(int warp, int i, int lane) { return warp * (32 * kItems) + i * 32 + lane; }
+// Items per thread so that the staged tile of all columns fits kStageBudget.
+int items_for(int64_t row_bytes) {
+    if (row_bytes * kThreads * 8 <= static_cast<int64_t>(kStageBudget)) return 8;
+    if (row_bytes * kThreads * 4 <= static_cast<int64_t>(kStageBudget)) return 4;
+    return 2;
+}
 
+// Local position of item i of this thread inside a tile: warp-contiguous runs of
+// 32 * ITEMS positions, lanes innermost, so position order = (warp, item, lane).
+template <int ITEMS>
+__device__ __forceinline__ int local_pos(int warp, int i, int lane) {
+    return warp * (32 * ITEMS) + i * 32 + lane;
+}
+
+template <int ITEMS>
 __global__ void __launch_bounds__(kThreads)
 part_hist_kernel(const int64_t* __restrict__ key, const int32_t* __restrict__ sel,
                  const int64_t* __restrict__ d_nsel, int64_t ncap, uint64_t seed, uint32_t nparts,
                  int32_t* __restrict__ cnt, int64_t ntiles) {
-    extern __shared__ int32_t s_hist[];
+    constexpr int T = kThreads * ITEMS;
+    extern __shared__ int32_t s_hist[];  // [kWarps][nparts]
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    for (uint32_t q = tid; q < nparts; q += kThreads) s_hist[q] = 0;
+    for (uint32_t q = tid; q < kWarps * nparts; q += kThreads) s_hist[q] = 0;
     const int64_t n = actual_rows(d_nsel, ncap);
-    const int64_t tbase = static_cast<int64_t>(blockIdx.x) * kTile;
-    uint32_t p[kItems];
+    const int64_t tbase = static_cast<int64_t>(blockIdx.x) * T;
+    uint32_t p[ITEMS];
 #pragma unroll
-    for (int i = 0; i < kItems; ++i) {
-        const int64_t j = tbase + local_pos(warp, i, lane);
+    for (int i = 0; i < ITEMS; ++i) {
+        const int64_t j = tbase + local_pos<ITEMS>(warp, i, lane);
         p[i] = nparts;
-        if (j < n) {
-            const int64_t r = sel ? static_cast<int64_t>(sel[j]) : j;
-            p[i] = part_of(key[r], seed, nparts);
-        }
+        if (j < n) p[i] = part_of(key[sel ? static_cast<int64_t>(sel[j]) : j], seed, nparts);
     }
     __syncthreads();
+    int32_t* wh = s_hist + warp * nparts;
 #pragma unroll
-    for (int i = 0; i < kItems; ++i) {
-        const uint32_t peers = __match_any_sync(FULL, p[i]);
-        if (p[i] < nparts && lane == __ffs(peers) - 1) atomicAdd(&s_hist[p[i]], __popc(peers));
-    }
+    for (int i = 0; i < ITEMS; ++i)
+        if (p[i] < nparts) atomicAdd(&wh[p[i]], 1);
     __syncthreads();
-    for (uint32_t q = tid; q < nparts; q += kThreads) cnt[static_cast<int64_t>(q) * ntiles + blockIdx.x] = s_hist[q];
+    for (uint32_t q = tid; q < nparts; q += kThreads) {
+        int32_t c = 0;
+        for (int w = 0; w < kWarps; ++w) c += s_hist[w * nparts + q];
+        cnt[static_cast<int64_t>(q) * ntiles + blockIdx.x] = c;
+    }
 }
 
 // Exclusive scan of cnt[0..total) (partition-major) into offs; offsets[q] is the
@@ -114,83 +132,130 @@ part_scan_kernel(const int32_t* __restrict__ cnt, int32_t* __restrict__ offs, in
     }
 }
 
-template <typename T>
-__device__ __forceinline__ void scatter_column(const Cols& cols, int c, bool is_key, const int64_t* keyv,
-                                               const int32_t* rowv, const uint32_t* pidv, const int32_t* posv,
-                                               uint32_t nparts, void* s_stage_raw, const uint16_t* s_pid,
-                                               const int32_t* s_delta, int tile_rows) {
-    T* s_stage = static_cast<T*>(s_stage_raw);
-    const T* in = static_cast<const T*>(cols.in[c]);
-    T val[kItems];
+// Moves one column's tile from the staging area (tile order) into partition order
+// in shared memory, then writes each partition's run to its global position.
+template <typename T, int ITEMS>
+__device__ __forceinline__ void scatter_col(const unsigned char* staged, void* sorted_raw, const uint16_t* s_pid,
+                                            const int32_t* s_delta, const int32_t* posv, const uint32_t* pidv,
+                                            uint32_t nparts, void* out, int tile_rows, int warp, int lane) {
+    const T* src = reinterpret_cast<const T*>(staged);
+    T* sorted = static_cast<T*>(sorted_raw);
+    T v[ITEMS];
 #pragma unroll
-    for (int i = 0; i < kItems; ++i)
-        if (pidv[i] < nparts) val[i] = is_key ? static_cast<T>(keyv[i]) : in[rowv[i]];
+    for (int i = 0; i < ITEMS; ++i)
+        if (pidv[i] < nparts) v[i] = src[local_pos<ITEMS>(warp, i, lane)];
 #pragma unroll
-    for (int i = 0; i < kItems; ++i)
-        if (pidv[i] < nparts) s_stage[posv[i]] = val[i];
+    for (int i = 0; i < ITEMS; ++i)
+        if (pidv[i] < nparts) sorted[posv[i]] = v[i];
     __syncthreads();
-    T* out = static_cast<T*>(cols.out[c]);
-    for (int j = threadIdx.x; j < tile_rows; j += kThreads)
-        out[static_cast<int64_t>(s_delta[s_pid[j]]) + j] = s_stage[j];
+    T* o = static_cast<T*>(out);
+    for (int j = threadIdx.x; j < tile_rows; j += kThreads) o[static_cast<int64_t>(s_delta[s_pid[j]]) + j] = sorted[j];
     __syncthreads();
 }
 
+template <typename T, int ITEMS>
+__device__ __forceinline__ void stage_plain(const T* in, T* staged, const int32_t* __restrict__ sel, int64_t tbase,
+                                            int tile_rows, int warp, int lane) {
+    T v[ITEMS];
+#pragma unroll
+    for (int i = 0; i < ITEMS; ++i) {
+        const int lp = local_pos<ITEMS>(warp, i, lane);
+        const int64_t j = tbase + lp;
+        if (lp < tile_rows) v[i] = in[sel ? static_cast<int64_t>(sel[j]) : j];
+    }
+#pragma unroll
+    for (int i = 0; i < ITEMS; ++i) {
+        const int lp = local_pos<ITEMS>(warp, i, lane);
+        if (lp < tile_rows) staged[lp] = v[i];
+    }
+}
+
+template <int ITEMS>
 __global__ void __launch_bounds__(kThreads)
 part_scatter_kernel(Cols cols, int32_t key_col, const int32_t* __restrict__ sel,
                     const int64_t* __restrict__ d_nsel, int64_t ncap, uint64_t seed, uint32_t nparts,
-                    const int32_t* __restrict__ offs, int64_t ntiles) {
+                    const int32_t* __restrict__ offs, int64_t ntiles, uint32_t stage_bytes, uint32_t row_bytes,
+                    int32_t* status) {
+    constexpr int T = kThreads * ITEMS;
     extern __shared__ __align__(16) unsigned char smem[];
     const int np1 = static_cast<int>(nparts) + 1;
-    int64_t* s_stage = reinterpret_cast<int64_t*>(smem);                       // kTile x 8 B
-    uint16_t* s_pid = reinterpret_cast<uint16_t*>(smem + kTile * 8);            // kTile
-    int32_t* s_warp = reinterpret_cast<int32_t*>(smem + kTile * 10);            // 33 (+3 pad)
-    int32_t* s_tstart = s_warp + 36;                                            // np1 (+pad)
-    int32_t* s_delta = s_tstart + ((np1 + 3) & ~3);                              // nparts (+pad)
-    int32_t* s_whist = s_delta + ((np1 + 3) & ~3);                               // kWarps x np1
+    const int np1p = (np1 + 3) & ~3;
+    unsigned char* stage = smem;                                                   // stage_bytes
+    void* sorted = smem + stage_bytes;                                             // T x 8 B
+    uint16_t* s_pid = reinterpret_cast<uint16_t*>(smem + stage_bytes + T * 8);    // T
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + stage_bytes + T * 10);     // 16 B
+    int32_t* s_warp = reinterpret_cast<int32_t*>(smem + stage_bytes + T * 10 + 16);  // 33 (+3)
+    int32_t* s_tstart = s_warp + 36;                                               // np1p
+    int32_t* s_delta = s_tstart + np1p;                                            // np1p
+    int32_t* s_whist = s_delta + np1p;                                             // kWarps x np1
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int64_t tile = blockIdx.x;
     const int64_t n = actual_rows(d_nsel, ncap);
-    const int64_t tbase = tile * kTile;
+    const int64_t tbase = tile * T;
     const int64_t rem = n - tbase;
-    const int tile_rows = rem <= 0 ? 0 : (rem < kTile ? static_cast<int>(rem) : kTile);
+    const int tile_rows = rem <= 0 ? 0 : (rem < T ? static_cast<int>(rem) : T);
     for (int k = tid; k < kWarps * np1; k += kThreads) s_whist[k] = 0;
 
-    const int64_t* key = static_cast<const int64_t*>(cols.in[key_col]);
-    int64_t keyv[kItems];
-    int32_t rowv[kItems];
-    uint32_t pidv[kItems];
-    int32_t posv[kItems];
-#pragma unroll
-    for (int i = 0; i < kItems; ++i) {
-        const int lp = local_pos(warp, i, lane);
-        pidv[i] = nparts;
-        rowv[i] = 0;
-        keyv[i] = 0;
-        if (lp < tile_rows) {
-            const int64_t j = tbase + lp;
-            rowv[i] = sel ? sel[j] : static_cast<int32_t>(j);
-            keyv[i] = key[rowv[i]];
+    // Stage the tile of every column: TMA bulk copies for a full contiguous tile,
+    // plain loads for a gather through a selection or a ragged last tile.
+    const bool bulk = sel == nullptr && tile_rows == T;
+    if (bulk) {
+        if (tid == 0) {
+            mbar_init(bar, 1);
+            fence_mbar_init();
         }
+        __syncthreads();
+        if (tid == 0) {
+            mbar_arrive_expect_tx(bar, static_cast<uint32_t>(T) * row_bytes);
+            for (int c = 0; c < cols.ncols; ++c)
+                bulk_g2s(stage + cols.stage_off[c], static_cast<const char*>(cols.in[c]) + tbase * cols.width[c],
+                         static_cast<uint32_t>(T * cols.width[c]), bar);
+        }
+        if (!mbar_wait(bar, 0) && lane == 0) set_status(status, PX_ERR_TIMEOUT);
+    } else {
+        for (int c = 0; c < cols.ncols; ++c) {
+            unsigned char* st = stage + cols.stage_off[c];
+            if (cols.width[c] == 8)
+                stage_plain<int64_t, ITEMS>(static_cast<const int64_t*>(cols.in[c]), reinterpret_cast<int64_t*>(st),
+                                            sel, tbase, tile_rows, warp, lane);
+            else if (cols.width[c] == 4)
+                stage_plain<int32_t, ITEMS>(static_cast<const int32_t*>(cols.in[c]), reinterpret_cast<int32_t*>(st),
+                                            sel, tbase, tile_rows, warp, lane);
+            else
+                stage_plain<int8_t, ITEMS>(static_cast<const int8_t*>(cols.in[c]), reinterpret_cast<int8_t*>(st), sel,
+                                           tbase, tile_rows, warp, lane);
+        }
+        __syncthreads();
     }
-#pragma unroll
-    for (int i = 0; i < kItems; ++i)
-        if (local_pos(warp, i, lane) < tile_rows) pidv[i] = part_of(keyv[i], seed, nparts);
-    __syncthreads();
 
-    // Stable rank inside the warp's run: rows of the same partition earlier in
-    // (item, lane) order, counted with match_any and a per-warp counter row.
+    // Partition of every row, then its stable rank inside the warp's run: the lanes
+    // with the same partition id come from one ballot per id bit (multi-split); a
+    // per-warp counter row carries ranks across the thread's items.
+    const int64_t* keys = reinterpret_cast<const int64_t*>(stage + cols.stage_off[key_col]);
+    uint32_t pidv[ITEMS];
+    int32_t posv[ITEMS];
+#pragma unroll
+    for (int i = 0; i < ITEMS; ++i) {
+        const int lp = local_pos<ITEMS>(warp, i, lane);
+        pidv[i] = lp < tile_rows ? part_of(keys[lp], seed, nparts) : nparts;
+    }
+    const int nbits = 32 - __clz(static_cast<int>(nparts));
     int32_t* wh = s_whist + warp * np1;
     const uint32_t lt = lanemask_lt();
 #pragma unroll
-    for (int i = 0; i < kItems; ++i) {
+    for (int i = 0; i < ITEMS; ++i) {
         const uint32_t p = pidv[i];
-        const uint32_t peers = __match_any_sync(FULL, p);
-        const int32_t b = wh[p];
+        uint32_t peers = FULL;
+        for (int b = 0; b < nbits; ++b) {
+            const uint32_t bal = __ballot_sync(FULL, (p >> b) & 1u);
+            peers &= ((p >> b) & 1u) ? bal : ~bal;
+        }
+        const int32_t base = wh[p];
         __syncwarp();
-        if (lane == __ffs(peers) - 1) wh[p] = b + __popc(peers);
+        if (lane == __ffs(peers) - 1) wh[p] = base + __popc(peers);
         __syncwarp();
-        posv[i] = b + __popc(peers & lt);
+        posv[i] = base + __popc(peers & lt);
     }
     __syncthreads();
     // Per partition: exclusive scan over warps (in place) and the tile's count.
@@ -208,7 +273,7 @@ part_scatter_kernel(Cols cols, int32_t key_col, const int32_t* __restrict__ sel,
     for (int q = tid; q < static_cast<int>(nparts); q += kThreads)
         s_delta[q] = offs[static_cast<int64_t>(q) * ntiles + tile] - s_tstart[q];
 #pragma unroll
-    for (int i = 0; i < kItems; ++i) {
+    for (int i = 0; i < ITEMS; ++i) {
         if (pidv[i] < nparts) {
             posv[i] += s_tstart[pidv[i]] + wh[pidv[i]];
             s_pid[posv[i]] = static_cast<uint16_t>(pidv[i]);
@@ -217,30 +282,33 @@ part_scatter_kernel(Cols cols, int32_t key_col, const int32_t* __restrict__ sel,
     __syncthreads();
 
     for (int c = 0; c < cols.ncols; ++c) {
-        const bool is_key = (c == key_col);
+        const unsigned char* st = stage + cols.stage_off[c];
         switch (cols.width[c]) {
             case 8:
-                scatter_column<int64_t>(cols, c, is_key, keyv, rowv, pidv, posv, nparts, s_stage, s_pid, s_delta,
-                                        tile_rows);
+                scatter_col<int64_t, ITEMS>(st, sorted, s_pid, s_delta, posv, pidv, nparts, cols.out[c], tile_rows,
+                                            warp, lane);
                 break;
             case 4:
-                scatter_column<int32_t>(cols, c, is_key, keyv, rowv, pidv, posv, nparts, s_stage, s_pid, s_delta,
-                                        tile_rows);
+                scatter_col<int32_t, ITEMS>(st, sorted, s_pid, s_delta, posv, pidv, nparts, cols.out[c], tile_rows,
+                                            warp, lane);
                 break;
             default:
-                scatter_column<int8_t>(cols, c, is_key, keyv, rowv, pidv, posv, nparts, s_stage, s_pid, s_delta,
-                                       tile_rows);
+                scatter_col<int8_t, ITEMS>(st, sorted, s_pid, s_delta, posv, pidv, nparts, cols.out[c], tile_rows,
+                                           warp, lane);
                 break;
         }
     }
 }
 
-size_t scatter_smem_bytes(int32_t nparts) {
+size_t scatter_smem_bytes(int items, uint32_t stage_bytes, int32_t nparts) {
+    const size_t T = static_cast<size_t>(kThreads) * items;
     const size_t np1 = static_cast<size_t>(nparts) + 1;
     const size_t np1p = (np1 + 3) & ~static_cast<size_t>(3);
-    return kTile * 10 + 36 * 4 + np1p * 4 * 2 + kWarps * np1 * 4;
+    return stage_bytes + T * 10 + 16 + 36 * 4 + np1p * 4 * 2 + kWarps * np1 * 4;
 }
 
+// Workspace: count matrix, offset matrix (partition-major, P x tiles int32) and the
+// scan scratch, sized for the smallest tile (2 items per thread).
 struct PartScratch {
     int32_t* cnt;
     int32_t* offs;
@@ -248,15 +316,49 @@ struct PartScratch {
     size_t scan_bytes;
 };
 
-PartScratch part_scratch(void* d_ws, int64_t ntiles, int32_t nparts) {
+size_t part_mat_bytes(int64_t nrows, int32_t nparts) {
+    return align_up(static_cast<size_t>(cdiv(nrows, kThreads * 2)) * nparts * 4, 256);
+}
+
+PartScratch part_scratch(void* d_ws, int64_t nrows, int64_t ntiles, int32_t nparts) {
     PartScratch p;
     char* base = static_cast<char*>(d_ws) + kWsScratch;
-    const size_t mat = align_up(static_cast<size_t>(ntiles) * nparts * 4, 256);
+    const size_t mat = part_mat_bytes(nrows, nparts);
     p.cnt = reinterpret_cast<int32_t*>(base);
     p.offs = reinterpret_cast<int32_t*>(base + mat);
     p.scan = base + 2 * mat;
     p.scan_bytes = scan_scratch_bytes(cdiv(ntiles * nparts, kScanTile));
     return p;
+}
+
+template <int ITEMS>
+px_status launch_partition(const Cols& cols, int32_t key_col, const int32_t* d_sel, const int64_t* d_n, int64_t ncap,
+                           uint64_t seed, int32_t nparts, int64_t* d_offsets, const PartScratch& ps, int64_t ntiles,
+                           uint32_t stage_bytes, uint32_t row_bytes, int32_t* status, cudaStream_t st) {
+    px_status s;
+    const int64_t* key = static_cast<const int64_t*>(cols.in[key_col]);
+    part_hist_kernel<ITEMS><<<static_cast<unsigned>(ntiles), kThreads, kWarps * nparts * sizeof(int32_t), st>>>(
+        key, d_sel, d_n, ncap, seed, static_cast<uint32_t>(nparts), ps.cnt, ntiles);
+    note_launch();
+    if ((s = check_launch("px_partition hist")) != PX_OK) return s;
+
+    const int64_t total = ntiles * nparts;
+    const int64_t nscan = cdiv(total, kScanTile);
+    cudaMemsetAsync(ps.scan, 0, ps.scan_bytes, st);
+    part_scan_kernel<<<static_cast<unsigned>(nscan), kScanThreads, 0, st>>>(
+        ps.cnt, ps.offs, total, ntiles, static_cast<uint32_t>(nparts), d_offsets, scan_scratch(ps.scan), status,
+        nscan);
+    note_launch();
+    if ((s = check_launch("px_partition scan")) != PX_OK) return s;
+
+    const size_t smem = scatter_smem_bytes(ITEMS, stage_bytes, nparts);
+    cudaFuncSetAttribute(part_scatter_kernel<ITEMS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         static_cast<int>(smem));
+    part_scatter_kernel<ITEMS><<<static_cast<unsigned>(ntiles), kThreads, smem, st>>>(
+        cols, key_col, d_sel, d_n, ncap, seed, static_cast<uint32_t>(nparts), ps.offs, ntiles, stage_bytes, row_bytes,
+        status);
+    note_launch();
+    return check_launch("px_partition scatter");
 }
 
 }  // namespace
@@ -269,9 +371,8 @@ extern "C" {
 size_t px_partition_ws_bytes(int64_t nrows, int32_t nparts) {
     if (nrows < 0) nrows = 0;
     if (nparts < 1) nparts = 1;
-    const int64_t ntiles = cdiv(nrows, kTile);
-    const size_t mat = align_up(static_cast<size_t>(ntiles) * nparts * 4, 256);
-    return kWsScratch + 2 * mat + scan_scratch_bytes(cdiv(ntiles * nparts, kScanTile));
+    const int64_t max_tiles = cdiv(nrows, kThreads * 2);
+    return kWsScratch + 2 * part_mat_bytes(nrows, nparts) + scan_scratch_bytes(cdiv(max_tiles * nparts, kScanTile));
 }
 
 px_status px_partition(const px_batch* in, int32_t key_col, const int32_t* d_sel, const int64_t* d_nsel,
@@ -306,40 +407,34 @@ px_status px_partition(const px_batch* in, int32_t key_col, const int32_t* d_sel
         cudaMemsetAsync(d_offsets, 0, sizeof(int64_t) * (nparts + 1), st);
         return check_launch("px_partition");
     }
-    const int64_t ntiles = cdiv(ncap, kTile);
-    const PartScratch ps = part_scratch(d_ws, ntiles, nparts);
-    int32_t* status = &static_cast<WsHeader*>(d_ws)->status;
-    const int64_t* d_n = d_sel ? d_nsel : in->d_nrows;
-    const int64_t* key = static_cast<const int64_t*>(in->cols[key_col].data);
-
-    part_hist_kernel<<<static_cast<unsigned>(ntiles), kThreads, nparts * sizeof(int32_t), st>>>(
-        key, d_sel, d_n, ncap, seed, static_cast<uint32_t>(nparts), ps.cnt, ntiles);
-    note_launch();
-    if ((s = check_launch("px_partition hist")) != PX_OK) return s;
-
-    const int64_t total = ntiles * nparts;
-    const int64_t nscan = cdiv(total, kScanTile);
-    cudaMemsetAsync(ps.scan, 0, ps.scan_bytes, st);
-    part_scan_kernel<<<static_cast<unsigned>(nscan), kScanThreads, 0, st>>>(
-        ps.cnt, ps.offs, total, ntiles, static_cast<uint32_t>(nparts), d_offsets, scan_scratch(ps.scan), status,
-        nscan);
-    note_launch();
-    if ((s = check_launch("px_partition scan")) != PX_OK) return s;
-
     Cols cols;
     cols.ncols = in->ncols;
+    uint32_t row_bytes = 0;
     for (int c = 0; c < in->ncols; ++c) {
         cols.width[c] = in->cols[c].type;
         cols.in[c] = in->cols[c].data;
         cols.out[c] = out->cols[c].data;
+        row_bytes += static_cast<uint32_t>(in->cols[c].type);
     }
-    const size_t smem = scatter_smem_bytes(nparts);
-    cudaFuncSetAttribute(part_scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         static_cast<int>(scatter_smem_bytes(PX_MAX_PARTS)));
-    part_scatter_kernel<<<static_cast<unsigned>(ntiles), kThreads, smem, st>>>(
-        cols, key_col, d_sel, d_n, ncap, seed, static_cast<uint32_t>(nparts), ps.offs, ntiles);
-    note_launch();
-    return check_launch("px_partition scatter");
+    const int items = items_for(row_bytes);
+    const int64_t T = static_cast<int64_t>(kThreads) * items;
+    uint32_t stage_bytes = 0;
+    for (int c = 0; c < in->ncols; ++c) {
+        cols.stage_off[c] = stage_bytes;
+        stage_bytes += static_cast<uint32_t>(align_up(static_cast<size_t>(T) * cols.width[c], 16));
+    }
+    const int64_t ntiles = cdiv(ncap, T);
+    const PartScratch ps = part_scratch(d_ws, ncap, ntiles, nparts);
+    int32_t* status = &static_cast<WsHeader*>(d_ws)->status;
+    const int64_t* d_n = d_sel ? d_nsel : in->d_nrows;
+    if (items == 8)
+        return launch_partition<8>(cols, key_col, d_sel, d_n, ncap, seed, nparts, d_offsets, ps, ntiles, stage_bytes,
+                                   row_bytes, status, st);
+    if (items == 4)
+        return launch_partition<4>(cols, key_col, d_sel, d_n, ncap, seed, nparts, d_offsets, ps, ntiles, stage_bytes,
+                                   row_bytes, status, st);
+    return launch_partition<2>(cols, key_col, d_sel, d_n, ncap, seed, nparts, d_offsets, ps, ntiles, stage_bytes,
+                               row_bytes, status, st);
 }
 
 }  // extern "C"
