@@ -288,4 +288,12 @@ px_status check_ws(const void* d_ws, size_t ws_bytes, size_t need, const char* w
 
 __host__ __device__ inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
+// Streaming multiprocessors of the current device.
+inline int sm_count() {
+    int dev = 0, n = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    return n > 0 ? n : 1;
+}
+
 }  // namespace px

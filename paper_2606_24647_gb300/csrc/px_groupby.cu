@@ -655,8 +655,12 @@ px_status launch_mode(const Spec& sp, size_t smem, const int32_t* sel, const int
     cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, smem);
+    // A dense block flushes its D slots into the global result at every segment end,
+    // so each block gets at least 4 D rows: fewer blocks for small inputs, whose
+    // flushes would otherwise pile same-address atomics onto the global array.
+    const int64_t min_rows = DENSE ? std::max<int64_t>(kTile, 4 * static_cast<int64_t>(sp.D)) : kTile;
     const int64_t grid = std::max<int64_t>(
-        1, std::min<int64_t>(cdiv(ncap, kTile), static_cast<int64_t>(num_sms()) * std::max(1, per_sm)));
+        1, std::min<int64_t>(cdiv(ncap, min_rows), static_cast<int64_t>(num_sms()) * std::max(1, per_sm)));
     kernel<<<static_cast<unsigned>(grid), kThreads, smem, st>>>(sp, sel, d_n, ncap, d_seg, g, max_groups, out_seg,
                                                                 status, hslots);
     note_launch();

@@ -10,7 +10,8 @@
 // every segment runs at load factor <= 1/2 and the whole table is exactly
 // 2 n + 2 nsegs slots with no size known before the build. A key's home slot is
 // the multiply-shift reduction of the LOWER 32 bits of fmix64(key) (the exchange
-// uses the upper 32), then linear probing. Empty slots hold INT64_MIN.
+// uses the upper 32) onto the segment's slot pairs, i.e. an even slot, then linear
+// probing. Empty slots hold INT64_MIN.
 #include <algorithm>
 
 #include "px_common.cuh"
@@ -50,6 +51,13 @@ TableView table_view(void* d_table, int32_t S) {
     t.seg = reinterpret_cast<int64_t*>(b + 64);
     t.slots = reinterpret_cast<Slot*>(b + 64 + seg_area_bytes(S));
     return t;
+}
+
+// Home slot of a key in a segment of `cap` slots (cap is even, segment bases are
+// even and the slot array is 64-byte aligned): an even slot, so the home slot and
+// its successor - the first two probes - share one aligned 32-byte sector.
+__device__ __forceinline__ uint32_t home_slot(uint64_t key, uint32_t cap) {
+    return 2 * slot_of(fmix64(key), cap / 2);
 }
 
 // ------------------------------------------------------------------ build ----
@@ -95,7 +103,7 @@ __global__ void build_insert_kernel(TableView t, int32_t S, int32_t unique, cons
     const int64_t s0 = t.seg[q], s1 = t.seg[q + 1];
     const int64_t base = 2 * s0 + 2 * static_cast<int64_t>(q);
     const uint32_t cap = static_cast<uint32_t>(2 * (s1 - s0) + 2);
-    uint32_t s = slot_of(fmix64(static_cast<uint64_t>(key)), cap);
+    uint32_t s = home_slot(static_cast<uint64_t>(key), cap);
     for (uint32_t probe = 0; probe < cap; ++probe) {
         Slot* slot = &t.slots[base + s];
         const unsigned long long prev = atomicCAS(reinterpret_cast<unsigned long long*>(&slot->key),
@@ -220,126 +228,139 @@ __device__ __forceinline__ int32_t count_matches(const Slot* seg_slots, uint32_t
     return m;
 }
 
-__global__ void __launch_bounds__(kThreads)
+constexpr int kMatchThreads = 256;
+constexpr int kMatchItems = kTile / kMatchThreads;  // 4 positions per thread per tile, same tile as emit
+
+// Keys of this thread's positions of tile `tile` (kEmpty where there is no row).
+__device__ __forceinline__ void match_keys(const int64_t* __restrict__ fk, const int32_t* __restrict__ sel,
+                                           int64_t n, bool bad, int64_t j0, int64_t* keyv) {
+#pragma unroll
+    for (int i = 0; i < kMatchItems; ++i) {
+        const int64_t j = j0 + 32 * i;
+        keyv[i] = (j < n && !bad) ? fk[sel ? static_cast<int64_t>(sel[j]) : j] : kEmpty;
+    }
+}
+
+// Persistent over tiles (grid-stride), software-pipelined: the next tile's keys
+// are loaded while the current tile's table slots are in flight. No block-wide
+// barrier: every thread reads the (cached) table header once and finds its own
+// segments; warps add their match counts atomically.
+__global__ void __launch_bounds__(kMatchThreads)
 probe_match_kernel(TableView t, int32_t S, const int64_t* __restrict__ fk, const int32_t* __restrict__ sel,
                    const int64_t* __restrict__ d_n, int64_t ncap, const int64_t* __restrict__ pseg,
                    int32_t* __restrict__ mrow, int32_t* __restrict__ tile_cnt, int32_t* status, int32_t npay,
-                   int64_t payload_rows) {
-    __shared__ int32_t s_bad, s_q0, s_unique;
-    __shared__ int32_t s_warp[kWarps];
-    const int64_t tile = blockIdx.x;
+                   int64_t payload_rows, int64_t ntiles) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t n = actual_rows(d_n, ncap);
-    if (threadIdx.x == 0) {
-        s_bad = (t.hdr->magic != kMagic || t.hdr->nsegs != S || (npay > 0 && t.hdr->nbuild > payload_rows)) ? 1 : 0;
-        if (s_bad && tile == 0) set_status(status, PX_ERR_INVALID);
-        s_unique = t.hdr->unique;
-        const int64_t p0 = tile * kTile;
-        s_q0 = (S > 1 && p0 < n) ? seg_of(pseg, S, p0) : 0;
-    }
-    __syncthreads();
-    const bool bad = s_bad != 0, unique = s_unique != 0;
-    int64_t j[kItems], keyv[kItems];
-    int32_t prow[kItems], out[kItems];
-    bool valid[kItems];
+    const bool bad = t.hdr->magic != kMagic || t.hdr->nsegs != S || (npay > 0 && t.hdr->nbuild > payload_rows);
+    if (bad && blockIdx.x == 0 && threadIdx.x == 0) set_status(status, PX_ERR_INVALID);
+    const bool unique = t.hdr->unique != 0;
+    const int64_t lane_off = warp * (32 * kMatchItems) + lane;  // item i of a tile at tile * kTile + lane_off + 32 i
+    int64_t tile = blockIdx.x;
+    if (tile >= ntiles) return;
+    int64_t keyv[kMatchItems];
+    match_keys(fk, sel, n, bad, tile * kTile + lane_off, keyv);
+    for (; tile < ntiles; tile += gridDim.x) {
+        const int64_t j0 = tile * kTile + lane_off;
+        int32_t out[kMatchItems];
+        // Segment of each position (monotone in i) and the home slot of its key.
+        int segq[kMatchItems];
+        uint32_t shome[kMatchItems];
+        {
+            int q = (S > 1 && j0 < n) ? seg_of(pseg, S, j0) : 0;
+            int64_t bound = (S > 1 && q + 1 < S) ? pseg[q + 1] : INT64_MAX;
+            int tq = -1;
+            uint32_t cap = 2;
 #pragma unroll
-    for (int i = 0; i < kItems; ++i) {
-        j[i] = tile_pos(tile, warp, i, lane);
-        valid[i] = j[i] < n && !bad;
-        prow[i] = valid[i] ? (sel ? sel[j[i]] : static_cast<int32_t>(j[i])) : 0;
-        out[i] = kNoMatch;
-    }
-#pragma unroll
-    for (int i = 0; i < kItems; ++i) keyv[i] = valid[i] ? fk[prow[i]] : kEmpty;
-    int segq[kItems];
-    segments_of(pseg, S, s_q0, j, valid, segq);
-    int64_t sbase[kItems];
-    uint32_t scap[kItems], shome[kItems];
-    {
-        int tq = -1;
-        int64_t t0 = 0, t1 = 0;
-#pragma unroll
-        for (int i = 0; i < kItems; ++i) {
-            sbase[i] = 0;
-            scap[i] = 1;
-            shome[i] = 0;
-            if (!valid[i] || keyv[i] == kEmpty) continue;
-            if (segq[i] != tq) {
-                tq = segq[i];
-                t0 = t.seg[tq];
-                t1 = t.seg[tq + 1];
-            }
-            sbase[i] = 2 * t0 + 2 * static_cast<int64_t>(tq);
-            scap[i] = static_cast<uint32_t>(2 * (t1 - t0) + 2);
-            shome[i] = slot_of(fmix64(static_cast<uint64_t>(keyv[i])), scap[i]);
-        }
-    }
-    int32_t cnt = 0;
-    if (unique) {
-        // The home slot and the next one for every item first (load factor <= 1/2
-        // settles most probes there), then continue only where both hold other keys.
-        longlong2 v0[kItems], v1[kItems];
-#pragma unroll
-        for (int i = 0; i < kItems; ++i) {
-            if (valid[i] && keyv[i] != kEmpty) {
-                const uint32_t s1 = shome[i] + 1 == scap[i] ? 0 : shome[i] + 1;
-                v0[i] = *reinterpret_cast<const longlong2*>(&t.slots[sbase[i] + shome[i]]);
-                v1[i] = *reinterpret_cast<const longlong2*>(&t.slots[sbase[i] + s1]);
-            } else {
-                v0[i] = make_longlong2(kEmpty, 0);
-                v1[i] = v0[i];
+            for (int i = 0; i < kMatchItems; ++i) {
+                const int64_t j = j0 + 32 * i;
+                out[i] = kNoMatch;
+                while (j >= bound) {
+                    ++q;
+                    bound = q + 1 < S ? pseg[q + 1] : INT64_MAX;
+                }
+                if (q != tq) {
+                    tq = q;
+                    cap = static_cast<uint32_t>(2 * (t.seg[q + 1] - t.seg[q]) + 2);
+                }
+                segq[i] = q;
+                shome[i] = home_slot(static_cast<uint64_t>(keyv[i]), cap);
             }
         }
+        int32_t cnt = 0;
+        if (unique) {
+            longlong2 v0[kMatchItems], v1[kMatchItems];
 #pragma unroll
-        for (int i = 0; i < kItems; ++i) {
-            if (!valid[i] || keyv[i] == kEmpty) continue;
-            const int64_t key = keyv[i];
-            if (v0[i].x == key) {
-                out[i] = static_cast<int32_t>(v0[i].y);
-            } else if (v0[i].x != kEmpty) {
-                if (v1[i].x == key) {
-                    out[i] = static_cast<int32_t>(v1[i].y);
-                } else if (v1[i].x != kEmpty) {
-                    const Slot* seg_slots = t.slots + sbase[i];
-                    uint32_t s = shome[i] + 2;
-                    if (s >= scap[i]) s -= scap[i];
-                    for (uint32_t probe = 2; probe < scap[i]; ++probe) {
-                        const longlong2 v = *reinterpret_cast<const longlong2*>(&seg_slots[s]);
-                        if (v.x == key) {
-                            out[i] = static_cast<int32_t>(v.y);
-                            break;
-                        }
-                        if (v.x == kEmpty) break;
-                        if (++s == scap[i]) s = 0;
-                    }
+            for (int i = 0; i < kMatchItems; ++i) {
+                if (keyv[i] != kEmpty) {
+                    const Slot* pair = t.slots + 2 * t.seg[segq[i]] + 2 * static_cast<int64_t>(segq[i]) + shome[i];
+                    v0[i] = *reinterpret_cast<const longlong2*>(pair);
+                    v1[i] = *reinterpret_cast<const longlong2*>(pair + 1);
+                } else {
+                    v0[i] = v1[i] = make_longlong2(kEmpty, 0);
                 }
             }
-            cnt += out[i] != kNoMatch ? 1 : 0;
-        }
-    } else {
-        // Multi-map: count every match; one match is recorded as its build row,
-        // several as -(global slot of the first + 2) for the emit pass to walk.
+            // Next tile's keys go out while this tile's slots are in flight.
+            int64_t keyn[kMatchItems];
+            match_keys(fk, sel, n, bad, (tile + gridDim.x) * kTile + lane_off, keyn);
 #pragma unroll
-        for (int i = 0; i < kItems; ++i) {
-            if (!valid[i] || keyv[i] == kEmpty) continue;
-            uint32_t first = 0;
-            const Slot* seg_slots = t.slots + sbase[i];
-            const int32_t m = count_matches(seg_slots, scap[i], shome[i], keyv[i], &first);
-            if (m == 1) out[i] = seg_slots[first].row;
-            else if (m > 1) out[i] = -static_cast<int32_t>(sbase[i] + first) - 2;
-            cnt += m;
-        }
-    }
+            for (int i = 0; i < kMatchItems; ++i) {
+                const int64_t key = keyv[i];
+                if (key == kEmpty) continue;
+                if (v0[i].x == key) {
+                    out[i] = static_cast<int32_t>(v0[i].y);
+                } else if (v0[i].x != kEmpty) {
+                    if (v1[i].x == key) {
+                        out[i] = static_cast<int32_t>(v1[i].y);
+                    } else if (v1[i].x != kEmpty) {
+                        // Rare: continue linear probing past the pair within the segment.
+                        const int q = segq[i];
+                        const int64_t t0 = t.seg[q], t1 = t.seg[q + 1];
+                        const Slot* seg_slots = t.slots + 2 * t0 + 2 * static_cast<int64_t>(q);
+                        const uint32_t cap = static_cast<uint32_t>(2 * (t1 - t0) + 2);
+                        uint32_t s = shome[i] + 2;
+                        if (s >= cap) s -= cap;
+                        for (uint32_t probe = 2; probe < cap; ++probe) {
+                            const longlong2 w = *reinterpret_cast<const longlong2*>(&seg_slots[s]);
+                            if (w.x == key) {
+                                out[i] = static_cast<int32_t>(w.y);
+                                break;
+                            }
+                            if (w.x == kEmpty) break;
+                            if (++s == cap) s = 0;
+                        }
+                    }
+                }
+                cnt += out[i] != kNoMatch ? 1 : 0;
+            }
 #pragma unroll
-    for (int i = 0; i < kItems; ++i)
-        if (j[i] < ncap) mrow[j[i]] = out[i];
-    cnt = warp_sum(cnt);
-    if (lane == 0) s_warp[warp] = cnt;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int32_t total = 0;
-        for (int w = 0; w < kWarps; ++w) total += s_warp[w];
-        tile_cnt[tile] = total;
+            for (int i = 0; i < kMatchItems; ++i) keyv[i] = keyn[i];
+        } else {
+            // Multi-map: count every match; one match is recorded as its build row,
+            // several as -(global slot of the first + 2) for the emit pass to walk.
+#pragma unroll
+            for (int i = 0; i < kMatchItems; ++i) {
+                if (keyv[i] == kEmpty) continue;
+                const int q = segq[i];
+                const int64_t t0 = t.seg[q], t1 = t.seg[q + 1];
+                const int64_t sb = 2 * t0 + 2 * static_cast<int64_t>(q);
+                const Slot* seg_slots = t.slots + sb;
+                const uint32_t cap = static_cast<uint32_t>(2 * (t1 - t0) + 2);
+                uint32_t first = 0;
+                const int32_t m = count_matches(seg_slots, cap, shome[i], keyv[i], &first);
+                if (m == 1) out[i] = seg_slots[first].row;
+                else if (m > 1) out[i] = -static_cast<int32_t>(sb + first) - 2;
+                cnt += m;
+            }
+            match_keys(fk, sel, n, bad, (tile + gridDim.x) * kTile + lane_off, keyv);
+        }
+#pragma unroll
+        for (int i = 0; i < kMatchItems; ++i) {
+            const int64_t j = j0 + 32 * i;
+            if (j < ncap) mrow[j] = out[i];
+        }
+        cnt = warp_sum(cnt);
+        if (lane == 0 && cnt) atomicAdd(&tile_cnt[tile], cnt);  // tile_cnt zeroed before the launch
     }
 }
 
@@ -396,7 +417,6 @@ probe_emit_kernel(TableView t, int32_t S, const int64_t* __restrict__ fk, const 
                   const int32_t* __restrict__ mrow, const int64_t* __restrict__ tile_off, OutCols oc,
                   int32_t* __restrict__ probe_row, int32_t* __restrict__ build_row, int64_t out_cap,
                   int64_t* __restrict__ d_out_seg) {
-    __shared__ int32_t s_q0;
     __shared__ int32_t s_warp[kWarps];
     const int64_t tile = blockIdx.x;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -414,13 +434,8 @@ probe_emit_kernel(TableView t, int32_t S, const int64_t* __restrict__ fk, const 
     // Matches per position: 1, 0, or (multi-map, -1 here) counted again below.
 #pragma unroll
     for (int i = 0; i < kItems; ++i) m[i] = mr[i] >= 0 ? 1 : (mr[i] == kNoMatch ? 0 : -1);
-    if (threadIdx.x == 0) {
-        const int64_t p0 = tile * kTile;
-        s_q0 = (S > 1 && p0 < n) ? seg_of(pseg, S, p0) : 0;
-    }
-    __syncthreads();
     int segq[kItems];
-    segments_of(pseg, S, s_q0, j, valid, segq);
+    segments_of(pseg, S, (S > 1 && valid[0]) ? seg_of(pseg, S, j[0]) : 0, j, valid, segq);
     int64_t key[kItems];
 #pragma unroll
     for (int i = 0; i < kItems; ++i) {
@@ -656,8 +671,12 @@ px_status px_join_probe(const void* d_table, const px_batch* probe, int32_t fk_c
     int32_t* status = &static_cast<WsHeader*>(d_ws)->status;
     const int64_t* fk = static_cast<const int64_t*>(probe->cols[fk_col].data);
     const unsigned grid = static_cast<unsigned>(L.ntiles);
-    probe_match_kernel<<<grid, kThreads, 0, st>>>(t, S, fk, d_sel, d_n, ncap, d_seg, mrow, tcnt, status, npay,
-                                                  build_payload ? build_payload->nrows : 0);
+    cudaMemsetAsync(tcnt, 0, 4 * static_cast<size_t>(L.ntiles), st);
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, probe_match_kernel, kMatchThreads, 0);
+    const unsigned mgrid = static_cast<unsigned>(std::min<int64_t>(L.ntiles, int64_t(sm_count()) * std::max(1, per_sm)));
+    probe_match_kernel<<<mgrid, kMatchThreads, 0, st>>>(t, S, fk, d_sel, d_n, ncap, d_seg, mrow, tcnt, status, npay,
+                                                        build_payload ? build_payload->nrows : 0, L.ntiles);
     note_launch();
     if ((s = check_launch("px_join_probe match")) != PX_OK) return s;
     cudaMemsetAsync(ws + L.scan, 0, scan_scratch_bytes(L.nscan), st);

@@ -134,10 +134,12 @@ part_scan_kernel(const int32_t* __restrict__ cnt, int32_t* __restrict__ offs, in
 
 // Moves one column's tile from the staging area (tile order) into partition order
 // in shared memory, then writes each partition's run to its global position.
+// dest[k]: global output row of partition-ordered position threadIdx.x + k * kThreads
+// of the tile (-1 past the tile), computed once and reused by every column.
 template <typename T, int ITEMS>
-__device__ __forceinline__ void scatter_col(const unsigned char* staged, void* sorted_raw, const uint16_t* s_pid,
-                                            const int32_t* s_delta, const int32_t* posv, const uint32_t* pidv,
-                                            uint32_t nparts, void* out, int tile_rows, int warp, int lane) {
+__device__ __forceinline__ void scatter_col(const unsigned char* staged, void* sorted_raw, const int32_t* dest,
+                                            const int32_t* posv, const uint32_t* pidv, uint32_t nparts, void* out,
+                                            int warp, int lane) {
     const T* src = reinterpret_cast<const T*>(staged);
     T* sorted = static_cast<T*>(sorted_raw);
     T v[ITEMS];
@@ -149,7 +151,9 @@ __device__ __forceinline__ void scatter_col(const unsigned char* staged, void* s
         if (pidv[i] < nparts) sorted[posv[i]] = v[i];
     __syncthreads();
     T* o = static_cast<T*>(out);
-    for (int j = threadIdx.x; j < tile_rows; j += kThreads) o[static_cast<int64_t>(s_delta[s_pid[j]]) + j] = sorted[j];
+#pragma unroll
+    for (int k = 0; k < ITEMS; ++k)
+        if (dest[k] >= 0) o[dest[k]] = sorted[threadIdx.x + k * kThreads];
     __syncthreads();
 }
 
@@ -171,7 +175,7 @@ __device__ __forceinline__ void stage_plain(const T* in, T* staged, const int32_
 }
 
 template <int ITEMS>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, 3)
 part_scatter_kernel(Cols cols, int32_t key_col, const int32_t* __restrict__ sel,
                     const int64_t* __restrict__ d_nsel, int64_t ncap, uint64_t seed, uint32_t nparts,
                     const int32_t* __restrict__ offs, int64_t ntiles, uint32_t stage_bytes, uint32_t row_bytes,
@@ -280,21 +284,24 @@ part_scatter_kernel(Cols cols, int32_t key_col, const int32_t* __restrict__ sel,
         }
     }
     __syncthreads();
+    int32_t dest[ITEMS];
+#pragma unroll
+    for (int k = 0; k < ITEMS; ++k) {
+        const int jj = tid + k * kThreads;
+        dest[k] = jj < tile_rows ? s_delta[s_pid[jj]] + jj : -1;
+    }
 
     for (int c = 0; c < cols.ncols; ++c) {
         const unsigned char* st = stage + cols.stage_off[c];
         switch (cols.width[c]) {
             case 8:
-                scatter_col<int64_t, ITEMS>(st, sorted, s_pid, s_delta, posv, pidv, nparts, cols.out[c], tile_rows,
-                                            warp, lane);
+                scatter_col<int64_t, ITEMS>(st, sorted, dest, posv, pidv, nparts, cols.out[c], warp, lane);
                 break;
             case 4:
-                scatter_col<int32_t, ITEMS>(st, sorted, s_pid, s_delta, posv, pidv, nparts, cols.out[c], tile_rows,
-                                            warp, lane);
+                scatter_col<int32_t, ITEMS>(st, sorted, dest, posv, pidv, nparts, cols.out[c], warp, lane);
                 break;
             default:
-                scatter_col<int8_t, ITEMS>(st, sorted, s_pid, s_delta, posv, pidv, nparts, cols.out[c], tile_rows,
-                                           warp, lane);
+                scatter_col<int8_t, ITEMS>(st, sorted, dest, posv, pidv, nparts, cols.out[c], warp, lane);
                 break;
         }
     }
