@@ -253,6 +253,19 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
         : "memory");
 }
 
+// ------------------------------------------------------------ reductions --
+// Fire-and-forget reductions (PTX red): no old value comes back, so the issuing
+// warp never waits on the memory system for them.
+__device__ __forceinline__ void red_add_global(unsigned long long* p, unsigned long long v) {
+    asm volatile("red.relaxed.gpu.global.add.u64 [%0], %1;" ::"l"(__cvta_generic_to_global(p)), "l"(v) : "memory");
+}
+__device__ __forceinline__ void red_add_shared(uint32_t* p, uint32_t v) {
+    asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(smem_u32(p)), "r"(v) : "memory");
+}
+__device__ __forceinline__ void red_or_shared(uint32_t* p, uint32_t v) {
+    asm volatile("red.shared.or.b32 [%0], %1;" ::"r"(smem_u32(p)), "r"(v) : "memory");
+}
+
 // Row count of a batch or selection: the device count when given (clamped to the
 // capacity), else the host count.
 __device__ __forceinline__ int64_t actual_rows(const int64_t* d_n, int64_t cap) {

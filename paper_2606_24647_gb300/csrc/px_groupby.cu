@@ -18,7 +18,7 @@
 // match_any), so a hot key costs one shared-memory update per warp, not 32.
 // The global table lives in the workspace: slots are claimed with a CAS on a
 // state word (empty -> claimed -> published), take the next output row from a
-// counter, and accumulate with 64-bit atomics straight into the output columns.
+// counter, and accumulate with 64-bit reductions straight into the output columns.
 // All arithmetic is mod 2^64. Every thread loads all of its rows' inputs for a
 // tile before aggregating any of them, so each thread keeps many loads in flight.
 #include <algorithm>
@@ -62,9 +62,10 @@ struct Spec {
     uint64_t span[PX_MAX_KEYS];
     // dense global result (when the whole (segment, key) space fits max_groups)
     int32_t dglobal;
+    int32_t direct;               // rows update the dense global array directly (no block arrays)
     uint64_t E;                   // entries: max(nsegs, 1) * D
     unsigned long long* dg_acc;   // [naggs][E]
-    uint32_t* dg_occ;             // [ceil(E / 32)] occupancy bits (only without COUNT)
+    uint8_t* dg_occ;              // [E] occupancy flags, 1 where the entry has rows (only without COUNT)
 };
 
 struct GTable {
@@ -152,7 +153,7 @@ __device__ __forceinline__ void global_add(const GTable& g, const Spec& sp, uint
     const int32_t gi = global_group(g, sp, code, max_groups, out_seg, status);
     if (gi < 0) return;
     for (int a = 0; a < sp.naggs; ++a)
-        atomicAdd(reinterpret_cast<unsigned long long*>(&sp.agg_out[a][gi]), static_cast<unsigned long long>(v[a]));
+        red_add_global(reinterpret_cast<unsigned long long*>(&sp.agg_out[a][gi]), static_cast<unsigned long long>(v[a]));
 }
 
 // Slot of `code` in the block's hash table, inserting it if absent; -1 if no
@@ -219,7 +220,7 @@ __device__ __forceinline__ void add_split_atomic(uint32_t* lo, uint32_t* hi, uin
     const uint32_t xl = static_cast<uint32_t>(x), xh = static_cast<uint32_t>(x >> 32);
     const uint32_t old = atomicAdd(lo, xl);
     const uint32_t add_hi = xh + (old + xl < old ? 1u : 0u);
-    if (add_hi) atomicAdd(hi, add_hi);
+    if (add_hi) red_add_shared(hi, add_hi);
 }
 __device__ __forceinline__ void add_split(uint32_t* lo, uint32_t* hi, uint64_t x) {
     const uint32_t xl = static_cast<uint32_t>(x), old = *lo;
@@ -274,8 +275,8 @@ __device__ void flush_block_table(const Spec& sp, const Smem& m, int q, const GT
                 // Dense global array: entry (segment q, slot d); no hashing, no claim.
                 const uint64_t e = static_cast<uint64_t>(q) * sp.D + d;
                 for (int a = 0; a < sp.naggs; ++a)
-                    atomicAdd(&sp.dg_acc[a * sp.E + e], static_cast<unsigned long long>(v[a]));
-                if (sp.count_agg < 0) atomicOr(&sp.dg_occ[e / 32], 1u << (e % 32));
+                    red_add_global(&sp.dg_acc[a * sp.E + e], static_cast<unsigned long long>(v[a]));
+                if (sp.count_agg < 0) sp.dg_occ[e] = 1;  // every writer stores the same value
                 continue;
             }
             const int64_t k0 = sp.lo[0] + static_cast<int64_t>(d / sp.span[1]);
@@ -323,17 +324,22 @@ __device__ __forceinline__ void load_col(const void* p, int w, const int32_t* ro
 // indices at load time, each aggregate is applied with one atomic per row (or a
 // plain add into the thread's private replica), rows outside the key range take
 // the global path afterwards.
-template <int NA>
+// DIRECT: no block arrays; every in-range row (or warp-combined hot key) adds
+// straight into the dense global array with 64-bit global reductions. Chosen for
+// inputs with few rows per entry, where block arrays would cost more to clear
+// and flush than they save (a Final merge of Partial results, say).
+template <int NA, bool DIRECT>
 __device__ void aggregate_range_dense(const Spec& sp, const Smem& m, const int32_t* __restrict__ sel, int64_t a0,
                                       int64_t a1, int q, const GTable& g, int64_t max_groups, int32_t* out_seg,
                                       int32_t* status) {
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const bool private_rep = sp.reps == kThreads;
+    const bool private_rep = !DIRECT && sp.reps == kThreads;
     const int rep = private_rep ? tid : warp % sp.reps;
-    uint32_t* const LO = rep_lo(sp, m, rep);
-    uint32_t* const HI = rep_hi(sp, m, rep);
-    uint32_t* const A32 = rep_u32(sp, m, rep);
-    uint32_t* const OCC = rep_occ(sp, m, rep);
+    uint32_t* const LO = DIRECT ? nullptr : rep_lo(sp, m, rep);
+    uint32_t* const HI = DIRECT ? nullptr : rep_hi(sp, m, rep);
+    uint32_t* const A32 = DIRECT ? nullptr : rep_u32(sp, m, rep);
+    uint32_t* const OCC = DIRECT ? nullptr : rep_occ(sp, m, rep);
+    const uint64_t ebase = static_cast<uint64_t>(q) * sp.D;
     for (int64_t tb = a0; tb < a1; tb += kTile) {
         int32_t row[kItems];
         uint32_t idx[kItems];
@@ -395,9 +401,22 @@ __device__ void aggregate_range_dense(const Spec& sp, const Smem& m, const int32
             }
         }
         // Apply in-range rows.
+        if (DIRECT) {
+#pragma unroll
+            for (int i = 0; i < kItems; ++i) {
+                if (apply[i] >= kIdxOutside) continue;
+                const uint64_t e = ebase + apply[i];
+#pragma unroll
+                for (int a = 0; a < NA; ++a) {
+                    if (a >= sp.naggs) break;
+                    red_add_global(&sp.dg_acc[a * sp.E + e], static_cast<unsigned long long>(v[a][i]));
+                }
+                if (sp.count_agg < 0) sp.dg_occ[e] = 1;  // every writer stores the same value
+            }
+        }
 #pragma unroll
         for (int a = 0; a < NA; ++a) {
-            if (a >= sp.naggs) break;
+            if (DIRECT || a >= sp.naggs) break;
             const size_t off = static_cast<size_t>(sp.slot[a]) * sp.D;
             if (sp.kind[a] == 0) {
 #pragma unroll
@@ -411,16 +430,16 @@ __device__ void aggregate_range_dense(const Spec& sp, const Smem& m, const int32
                 for (int i = 0; i < kItems; ++i) {
                     if (apply[i] >= kIdxOutside) continue;
                     if (private_rep) A32[off + apply[i]] += static_cast<uint32_t>(v[a][i]);
-                    else atomicAdd(&A32[off + apply[i]], static_cast<uint32_t>(v[a][i]));
+                    else red_add_shared(&A32[off + apply[i]], static_cast<uint32_t>(v[a][i]));
                 }
             }
         }
-        if (sp.count_agg < 0) {
+        if (!DIRECT && sp.count_agg < 0) {
 #pragma unroll
             for (int i = 0; i < kItems; ++i) {
                 if (apply[i] >= kIdxOutside) continue;
                 if (private_rep) OCC[apply[i] / 32] |= 1u << (apply[i] % 32);
-                else atomicOr(&OCC[apply[i] / 32], 1u << (apply[i] % 32));
+                else red_or_shared(&OCC[apply[i] / 32], 1u << (apply[i] % 32));
             }
         }
         // Rows outside the key range (rare when the statistic is right): global path.
@@ -515,27 +534,32 @@ __device__ void aggregate_range(const Spec& sp, const Smem& m, const int32_t* __
     }
 }
 
-// DENSE must equal sp.dense: the two modes are separate kernels so each gets its
-// own register allocation.
-template <int NA, bool DENSE>
+// Modes: kHashed, kDenseBlock (block arrays) and kDenseDirect (rows straight into
+// the dense global array). MODE must agree with sp.dense / sp.direct: the modes are
+// separate kernels so each gets its own register allocation.
+constexpr int kHashed = 0, kDenseBlock = 1, kDenseDirect = 2;
+
+template <int NA, int MODE>
 __global__ void __launch_bounds__(kThreads)
 groupby_kernel(Spec sp, const int32_t* __restrict__ sel, const int64_t* __restrict__ d_n, int64_t ncap,
                const int64_t* __restrict__ d_seg, GTable g, int64_t max_groups, int32_t* __restrict__ out_seg,
                int32_t* status, uint32_t hash_slots) {
     extern __shared__ __align__(16) unsigned char smem[];
-    Smem m;
-    if (DENSE) {
+    Smem m = {};
+    if (MODE == kDenseBlock) {
         m.rep0 = smem;
         m.occ_words = (sp.D + 31) / 32;
-    } else {
+    } else if (MODE == kHashed) {
         m.S = hash_slots;
         m.h_lo = reinterpret_cast<uint32_t*>(smem);
         m.h_hi = m.h_lo + static_cast<size_t>(sp.naggs) * hash_slots;
         m.h_key = reinterpret_cast<unsigned long long*>(m.h_hi + static_cast<size_t>(sp.naggs) * hash_slots);
         m.h_state = reinterpret_cast<uint32_t*>(m.h_key + hash_slots);
     }
-    clear_block_table(sp, m);
-    __syncthreads();
+    if (MODE != kDenseDirect) {
+        clear_block_table(sp, m);
+        __syncthreads();
+    }
 
     const int64_t n = actual_rows(d_n, ncap);
     const int64_t chunk = cdiv(cdiv(n, gridDim.x), kTile) * kTile;
@@ -552,9 +576,15 @@ groupby_kernel(Spec sp, const int32_t* __restrict__ sel, const int64_t* __restri
                 if (e > pos && e < ce) qend = e;
             }
         }
-        if (DENSE) aggregate_range_dense<NA>(sp, m, sel, pos, qend, q, g, max_groups, out_seg, status);
-        else aggregate_range<NA>(sp, m, sel, pos, qend, q, g, max_groups, out_seg, status);
-        flush_block_table(sp, m, q, g, max_groups, out_seg, status);
+        if (MODE == kDenseDirect) {
+            aggregate_range_dense<NA, true>(sp, m, sel, pos, qend, q, g, max_groups, out_seg, status);
+        } else {
+            if (MODE == kDenseBlock)
+                aggregate_range_dense<NA, false>(sp, m, sel, pos, qend, q, g, max_groups, out_seg, status);
+            else
+                aggregate_range<NA>(sp, m, sel, pos, qend, q, g, max_groups, out_seg, status);
+            flush_block_table(sp, m, q, g, max_groups, out_seg, status);
+        }
         pos = qend;
     }
 }
@@ -586,7 +616,7 @@ dense_emit_kernel(Spec sp, const unsigned long long* __restrict__ ngroups_hash, 
         const int64_t e = base + i * 32 + lane;
         bool occ = false;
         if (e < E)
-            occ = sp.count_agg >= 0 ? sp.dg_acc[sp.count_agg * E + e] != 0 : ((sp.dg_occ[e / 32] >> (e % 32)) & 1u);
+            occ = sp.count_agg >= 0 ? sp.dg_acc[sp.count_agg * E + e] != 0 : sp.dg_occ[e] != 0;
         mask[i] = __ballot_sync(FULL, occ);
         cnt += __popc(mask[i]);
     }
@@ -647,18 +677,19 @@ int num_sms() {
     return n > 0 ? n : 1;
 }
 
-template <int NA, bool DENSE>
+template <int NA, int MODE>
 px_status launch_mode(const Spec& sp, size_t smem, const int32_t* sel, const int64_t* d_n, int64_t ncap,
                       const int64_t* d_seg, const GTable& g, int64_t max_groups, int32_t* out_seg, int32_t* status,
                       uint32_t hslots, cudaStream_t st) {
-    auto kernel = groupby_kernel<NA, DENSE>;
+    auto kernel = groupby_kernel<NA, MODE>;
     cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, smem);
     // A dense block flushes its D slots into the global result at every segment end,
     // so each block gets at least 4 D rows: fewer blocks for small inputs, whose
     // flushes would otherwise pile same-address atomics onto the global array.
-    const int64_t min_rows = DENSE ? std::max<int64_t>(kTile, 4 * static_cast<int64_t>(sp.D)) : kTile;
+    const int64_t min_rows =
+        MODE == kDenseBlock ? std::max<int64_t>(kTile, 4 * static_cast<int64_t>(sp.D)) : kTile;
     const int64_t grid = std::max<int64_t>(
         1, std::min<int64_t>(cdiv(ncap, min_rows), static_cast<int64_t>(num_sms()) * std::max(1, per_sm)));
     kernel<<<static_cast<unsigned>(grid), kThreads, smem, st>>>(sp, sel, d_n, ncap, d_seg, g, max_groups, out_seg,
@@ -671,8 +702,13 @@ template <int NA>
 px_status launch(const Spec& sp, size_t smem, const int32_t* sel, const int64_t* d_n, int64_t ncap,
                  const int64_t* d_seg, const GTable& g, int64_t max_groups, int32_t* out_seg, int32_t* status,
                  uint32_t hslots, cudaStream_t st) {
-    if (sp.dense) return launch_mode<NA, true>(sp, smem, sel, d_n, ncap, d_seg, g, max_groups, out_seg, status, hslots, st);
-    return launch_mode<NA, false>(sp, smem, sel, d_n, ncap, d_seg, g, max_groups, out_seg, status, hslots, st);
+    if (sp.direct)
+        return launch_mode<NA, kDenseDirect>(sp, smem, sel, d_n, ncap, d_seg, g, max_groups, out_seg, status, hslots,
+                                             st);
+    if (sp.dense)
+        return launch_mode<NA, kDenseBlock>(sp, smem, sel, d_n, ncap, d_seg, g, max_groups, out_seg, status, hslots,
+                                            st);
+    return launch_mode<NA, kHashed>(sp, smem, sel, d_n, ncap, d_seg, g, max_groups, out_seg, status, hslots, st);
 }
 
 }  // namespace
@@ -683,7 +719,7 @@ using namespace px;
 extern "C" {
 
 // Workspace: [header][group counter][hash table: state, key, gidx (G slots)]
-// [dense global: acc (PX_MAX_AGGS x max_groups), occupancy bits][emit scan scratch].
+// [dense global: acc (PX_MAX_AGGS x max_groups), occupancy flags (1 byte each)][emit scan scratch].
 struct WsLayout {
     size_t counter, state, key, gidx, dg_acc, dg_occ, emit_scan, total;
 };
@@ -699,7 +735,7 @@ WsLayout ws_layout(int64_t max_groups) {
     L.gidx = L.key + align_up(8 * G, 256);
     L.dg_acc = L.gidx + align_up(4 * G, 256);
     L.dg_occ = L.dg_acc + align_up(8 * PX_MAX_AGGS * M, 256);
-    L.emit_scan = L.dg_occ + align_up((M + 31) / 32 * 4, 256);
+    L.emit_scan = L.dg_occ + align_up(M, 256);
     L.total = L.emit_scan + scan_scratch_bytes(cdiv(static_cast<int64_t>(M), kEmitTile));
     return L;
 }
@@ -782,9 +818,14 @@ px_status px_groupby_agg(const px_batch* in, const int32_t* key_cols, int32_t nk
     s = check_ws(d_ws, ws_bytes, px_groupby_ws_bytes(in->nrows, max_groups), "px_groupby_agg");
     if (s != PX_OK) return s;
 
-    // Dense block arrays when the key statistic makes the key space small enough.
+    // Dense modes when the key statistic makes the key space small enough: rows go
+    // straight into a dense global array when every (segment, key) entry fits
+    // max_groups and there are too few rows to give each SM a block that amortises
+    // clearing and flushing D block slots; else dense block arrays when they fit
+    // shared memory; else hashing.
     size_t smem = 0;
     sp.dense = 0;
+    sp.direct = 0;
     sp.reps = 1;
     sp.span[0] = sp.span[1] = 1;
     if (range) {
@@ -810,7 +851,14 @@ px_status px_groupby_agg(const px_batch* in, const int32_t* key_cols, int32_t nk
             size_t per_rep = static_cast<size_t>(sp.n64) * D * 8 + static_cast<size_t>(sp.n32) * D * 4 +
                              (sp.count_agg < 0 ? (D + 31) / 32 * 4 : 0);
             per_rep = align_up(per_rep, 8);
-            if (per_rep > 0 && per_rep <= kSmemBudget) {
+            const uint64_t E = static_cast<uint64_t>(nsegs > 0 ? nsegs : 1) * D;
+            const bool few_rows =
+                cdiv(in->nrows, std::max<int64_t>(kTile, 4 * static_cast<int64_t>(D))) < num_sms();
+            if (E <= static_cast<uint64_t>(max_groups) && few_rows) {
+                sp.dense = 1;
+                sp.direct = 1;
+                sp.D = static_cast<uint32_t>(D);
+            } else if (per_rep > 0 && per_rep <= kSmemBudget) {
                 sp.dense = 1;
                 sp.D = static_cast<uint32_t>(D);
                 // One replica per thread when they fit (plain adds, no contention),
@@ -851,9 +899,9 @@ px_status px_groupby_agg(const px_batch* in, const int32_t* key_cols, int32_t nk
             sp.dglobal = 1;
             sp.E = E;
             sp.dg_acc = reinterpret_cast<unsigned long long*>(ws + L.dg_acc);
-            sp.dg_occ = reinterpret_cast<uint32_t*>(ws + L.dg_occ);
+            sp.dg_occ = reinterpret_cast<uint8_t*>(ws + L.dg_occ);
             cudaMemsetAsync(sp.dg_acc, 0, 8ull * naggs * E, st);
-            if (sp.count_agg < 0) cudaMemsetAsync(sp.dg_occ, 0, (E + 31) / 32 * 4, st);
+            if (sp.count_agg < 0) cudaMemsetAsync(sp.dg_occ, 0, E, st);
         }
     }
     const int64_t ncap = in->nrows;

@@ -192,24 +192,6 @@ __device__ __forceinline__ int64_t tile_pos(int64_t tile, int warp, int i, int l
     return tile * kTile + warp * (32 * kItems) + i * 32 + lane;
 }
 
-// Segment of each valid position, advancing monotonically from q0 (the segment of
-// the tile's first position); positions of a thread increase with i.
-__device__ __forceinline__ void segments_of(const int64_t* pseg, int S, int q0, const int64_t* j, const bool* valid,
-                                            int* segq) {
-    int q = q0;
-    int64_t bound = (S > 1 && q + 1 < S) ? pseg[q + 1] : INT64_MAX;
-#pragma unroll
-    for (int i = 0; i < kItems; ++i) {
-        segq[i] = q;
-        if (!valid[i]) continue;
-        while (j[i] >= bound) {
-            ++q;
-            bound = q + 1 < S ? pseg[q + 1] : INT64_MAX;
-        }
-        segq[i] = q;
-    }
-}
-
 // Number of matches of `key` along the probe sequence from `s` in one segment's
 // slots, and the slot of the first one.
 __device__ __forceinline__ int32_t count_matches(const Slot* seg_slots, uint32_t cap, uint32_t s, int64_t key,
@@ -233,19 +215,50 @@ constexpr int kMatchItems = kTile / kMatchThreads;  // 4 positions per thread pe
 
 // Keys of this thread's positions of tile `tile` (kEmpty where there is no row).
 __device__ __forceinline__ void match_keys(const int64_t* __restrict__ fk, const int32_t* __restrict__ sel,
-                                           int64_t n, bool bad, int64_t j0, int64_t* keyv) {
+                                           int64_t n, int64_t j0, int64_t* keyv) {
 #pragma unroll
     for (int i = 0; i < kMatchItems; ++i) {
         const int64_t j = j0 + 32 * i;
-        keyv[i] = (j < n && !bad) ? fk[sel ? static_cast<int64_t>(sel[j]) : j] : kEmpty;
+        keyv[i] = j < n ? fk[sel ? static_cast<int64_t>(sel[j]) : j] : kEmpty;
     }
+}
+
+// Segment cursor of one thread: segment q holds the thread's latest position,
+// `end` is where q's positions end, sb/cap locate q's table slots. A thread's
+// positions only increase, so the cursor only moves forward.
+struct SegCursor {
+    int q;
+    int64_t end;
+    int64_t sb;
+    uint32_t cap;
+};
+
+__device__ __forceinline__ void cursor_table(SegCursor& c, const TableView& t) {
+    const int64_t t0 = t.seg[c.q], t1 = t.seg[c.q + 1];
+    c.sb = 2 * t0 + 2 * static_cast<int64_t>(c.q);
+    c.cap = static_cast<uint32_t>(2 * (t1 - t0) + 2);
+}
+
+__device__ __forceinline__ void cursor_init(SegCursor& c, const TableView& t, const int64_t* pseg, int S, int64_t j) {
+    c.q = S > 1 ? seg_of(pseg, S, j) : 0;
+    c.end = c.q + 1 < S ? pseg[c.q + 1] : INT64_MAX;
+    cursor_table(c, t);
+}
+
+__device__ __forceinline__ void cursor_seek(SegCursor& c, const TableView& t, const int64_t* pseg, int S, int64_t j) {
+    if (j < c.end) return;
+    do {
+        ++c.q;
+        c.end = c.q + 1 < S ? pseg[c.q + 1] : INT64_MAX;
+    } while (j >= c.end);
+    cursor_table(c, t);
 }
 
 // Persistent over tiles (grid-stride), software-pipelined: the next tile's keys
 // are loaded while the current tile's table slots are in flight. No block-wide
-// barrier: every thread reads the (cached) table header once and finds its own
-// segments; warps add their match counts atomically.
-__global__ void __launch_bounds__(kMatchThreads)
+// barrier: every thread reads the (cached) table header once and follows its own
+// segment cursor; warps add their match counts atomically.
+__global__ void __launch_bounds__(kMatchThreads, 4)
 probe_match_kernel(TableView t, int32_t S, const int64_t* __restrict__ fk, const int32_t* __restrict__ sel,
                    const int64_t* __restrict__ d_n, int64_t ncap, const int64_t* __restrict__ pseg,
                    int32_t* __restrict__ mrow, int32_t* __restrict__ tile_cnt, int32_t* status, int32_t npay,
@@ -258,51 +271,38 @@ probe_match_kernel(TableView t, int32_t S, const int64_t* __restrict__ fk, const
     const int64_t lane_off = warp * (32 * kMatchItems) + lane;  // item i of a tile at tile * kTile + lane_off + 32 i
     int64_t tile = blockIdx.x;
     if (tile >= ntiles) return;
+    const int64_t nv = bad ? 0 : n;  // positions with a key to look up
+    SegCursor c;
+    cursor_init(c, t, pseg, S, tile * kTile + lane_off);
     int64_t keyv[kMatchItems];
-    match_keys(fk, sel, n, bad, tile * kTile + lane_off, keyv);
+    match_keys(fk, sel, nv, tile * kTile + lane_off, keyv);
     for (; tile < ntiles; tile += gridDim.x) {
         const int64_t j0 = tile * kTile + lane_off;
         int32_t out[kMatchItems];
-        // Segment of each position (monotone in i) and the home slot of its key.
         int segq[kMatchItems];
-        uint32_t shome[kMatchItems];
-        {
-            int q = (S > 1 && j0 < n) ? seg_of(pseg, S, j0) : 0;
-            int64_t bound = (S > 1 && q + 1 < S) ? pseg[q + 1] : INT64_MAX;
-            int tq = -1;
-            uint32_t cap = 2;
+        const Slot* pair[kMatchItems];
 #pragma unroll
-            for (int i = 0; i < kMatchItems; ++i) {
-                const int64_t j = j0 + 32 * i;
-                out[i] = kNoMatch;
-                while (j >= bound) {
-                    ++q;
-                    bound = q + 1 < S ? pseg[q + 1] : INT64_MAX;
-                }
-                if (q != tq) {
-                    tq = q;
-                    cap = static_cast<uint32_t>(2 * (t.seg[q + 1] - t.seg[q]) + 2);
-                }
-                segq[i] = q;
-                shome[i] = home_slot(static_cast<uint64_t>(keyv[i]), cap);
-            }
+        for (int i = 0; i < kMatchItems; ++i) {
+            cursor_seek(c, t, pseg, S, j0 + 32 * i);
+            segq[i] = c.q;
+            pair[i] = t.slots + c.sb + home_slot(static_cast<uint64_t>(keyv[i]), c.cap);
+            out[i] = kNoMatch;
         }
-        int32_t cnt = 0;
         if (unique) {
             longlong2 v0[kMatchItems], v1[kMatchItems];
 #pragma unroll
             for (int i = 0; i < kMatchItems; ++i) {
                 if (keyv[i] != kEmpty) {
-                    const Slot* pair = t.slots + 2 * t.seg[segq[i]] + 2 * static_cast<int64_t>(segq[i]) + shome[i];
-                    v0[i] = *reinterpret_cast<const longlong2*>(pair);
-                    v1[i] = *reinterpret_cast<const longlong2*>(pair + 1);
+                    v0[i] = *reinterpret_cast<const longlong2*>(pair[i]);
+                    v1[i] = *reinterpret_cast<const longlong2*>(pair[i] + 1);
                 } else {
                     v0[i] = v1[i] = make_longlong2(kEmpty, 0);
                 }
             }
             // Next tile's keys go out while this tile's slots are in flight.
             int64_t keyn[kMatchItems];
-            match_keys(fk, sel, n, bad, (tile + gridDim.x) * kTile + lane_off, keyn);
+            match_keys(fk, sel, nv, (tile + gridDim.x) * kTile + lane_off, keyn);
+            uint32_t hits = 0;
 #pragma unroll
             for (int i = 0; i < kMatchItems; ++i) {
                 const int64_t key = keyv[i];
@@ -318,7 +318,7 @@ probe_match_kernel(TableView t, int32_t S, const int64_t* __restrict__ fk, const
                         const int64_t t0 = t.seg[q], t1 = t.seg[q + 1];
                         const Slot* seg_slots = t.slots + 2 * t0 + 2 * static_cast<int64_t>(q);
                         const uint32_t cap = static_cast<uint32_t>(2 * (t1 - t0) + 2);
-                        uint32_t s = shome[i] + 2;
+                        uint32_t s = static_cast<uint32_t>(pair[i] - seg_slots) + 2;
                         if (s >= cap) s -= cap;
                         for (uint32_t probe = 2; probe < cap; ++probe) {
                             const longlong2 w = *reinterpret_cast<const longlong2*>(&seg_slots[s]);
@@ -331,13 +331,17 @@ probe_match_kernel(TableView t, int32_t S, const int64_t* __restrict__ fk, const
                         }
                     }
                 }
-                cnt += out[i] != kNoMatch ? 1 : 0;
             }
 #pragma unroll
-            for (int i = 0; i < kMatchItems; ++i) keyv[i] = keyn[i];
+            for (int i = 0; i < kMatchItems; ++i) {
+                hits += __popc(__ballot_sync(FULL, out[i] != kNoMatch));
+                keyv[i] = keyn[i];
+            }
+            if (lane == 0 && hits) atomicAdd(&tile_cnt[tile], static_cast<int32_t>(hits));  // zeroed before launch
         } else {
             // Multi-map: count every match; one match is recorded as its build row,
             // several as -(global slot of the first + 2) for the emit pass to walk.
+            int32_t cnt = 0;
 #pragma unroll
             for (int i = 0; i < kMatchItems; ++i) {
                 if (keyv[i] == kEmpty) continue;
@@ -347,20 +351,21 @@ probe_match_kernel(TableView t, int32_t S, const int64_t* __restrict__ fk, const
                 const Slot* seg_slots = t.slots + sb;
                 const uint32_t cap = static_cast<uint32_t>(2 * (t1 - t0) + 2);
                 uint32_t first = 0;
-                const int32_t m = count_matches(seg_slots, cap, shome[i], keyv[i], &first);
+                const int32_t m =
+                    count_matches(seg_slots, cap, static_cast<uint32_t>(pair[i] - seg_slots), keyv[i], &first);
                 if (m == 1) out[i] = seg_slots[first].row;
                 else if (m > 1) out[i] = -static_cast<int32_t>(sb + first) - 2;
                 cnt += m;
             }
-            match_keys(fk, sel, n, bad, (tile + gridDim.x) * kTile + lane_off, keyv);
+            match_keys(fk, sel, nv, (tile + gridDim.x) * kTile + lane_off, keyv);
+            cnt = warp_sum(cnt);
+            if (lane == 0 && cnt) atomicAdd(&tile_cnt[tile], cnt);  // tile_cnt zeroed before the launch
         }
 #pragma unroll
         for (int i = 0; i < kMatchItems; ++i) {
             const int64_t j = j0 + 32 * i;
             if (j < ncap) mrow[j] = out[i];
         }
-        cnt = warp_sum(cnt);
-        if (lane == 0 && cnt) atomicAdd(&tile_cnt[tile], cnt);  // tile_cnt zeroed before the launch
     }
 }
 
@@ -418,9 +423,12 @@ probe_emit_kernel(TableView t, int32_t S, const int64_t* __restrict__ fk, const 
                   int32_t* __restrict__ probe_row, int32_t* __restrict__ build_row, int64_t out_cap,
                   int64_t* __restrict__ d_out_seg) {
     __shared__ int32_t s_warp[kWarps];
+    __shared__ int32_t s_q0;
     const int64_t tile = blockIdx.x;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t n = actual_rows(d_n, ncap);
+    // One thread finds the segment of the tile's first position for everyone.
+    if (d_out_seg && threadIdx.x == 0) s_q0 = (S > 1 && tile * kTile < n) ? seg_of(pseg, S, tile * kTile) : 0;
     int64_t j[kItems];
     int32_t mr[kItems], prow[kItems], m[kItems];
     bool valid[kItems];
@@ -431,18 +439,14 @@ probe_emit_kernel(TableView t, int32_t S, const int64_t* __restrict__ fk, const 
         mr[i] = valid[i] ? mrow[j[i]] : kNoMatch;
         prow[i] = valid[i] ? (sel ? sel[j[i]] : static_cast<int32_t>(j[i])) : 0;
     }
-    // Matches per position: 1, 0, or (multi-map, -1 here) counted again below.
-#pragma unroll
-    for (int i = 0; i < kItems; ++i) m[i] = mr[i] >= 0 ? 1 : (mr[i] == kNoMatch ? 0 : -1);
-    int segq[kItems];
-    segments_of(pseg, S, (S > 1 && valid[0]) ? seg_of(pseg, S, j[0]) : 0, j, valid, segq);
+    // Matches per position: 1, 0, or (multi-map) counted again along the chain.
     int64_t key[kItems];
 #pragma unroll
     for (int i = 0; i < kItems; ++i) {
+        m[i] = mr[i] >= 0 ? 1 : 0;
         key[i] = 0;
-        if (m[i] >= 0) continue;
-        // Multi-map: count the matches along the probe chain from the first one.
-        const int q = segq[i];
+        if (mr[i] >= kNoMatch) continue;
+        const int q = S > 1 ? seg_of(pseg, S, j[i]) : 0;
         const int64_t t0 = t.seg[q], t1 = t.seg[q + 1];
         const int64_t sb = 2 * t0 + 2 * static_cast<int64_t>(q);
         const uint32_t cap = static_cast<uint32_t>(2 * (t1 - t0) + 2);
@@ -472,8 +476,23 @@ probe_emit_kernel(TableView t, int32_t S, const int64_t* __restrict__ fk, const 
     for (int i = 0; i < kItems; ++i) {
         pos[i] = base + pre[i];
         one[i] = mr[i] >= 0 && pos[i] < out_cap;
-        if (d_out_seg && valid[i]) {
-            for (int q = segq[i]; q >= 0 && (S > 1 ? pseg[q] == j[i] : j[i] == 0); --q) d_out_seg[q] = pos[i];
+    }
+    if (d_out_seg) {
+        // A position where segments start (several when some are empty) gives those
+        // segments their first output row; a forward cursor over the segment starts.
+        int q = s_q0;
+        int64_t start = S > 1 ? pseg[q] : 0;
+        int64_t end = q + 1 < S ? pseg[q + 1] : INT64_MAX;
+#pragma unroll
+        for (int i = 0; i < kItems; ++i) {
+            if (!valid[i]) continue;
+            while (j[i] >= end) {
+                ++q;
+                start = end;
+                end = q + 1 < S ? pseg[q + 1] : INT64_MAX;
+            }
+            if (j[i] == start)
+                for (int r = q; r >= 0 && (S > 1 ? pseg[r] == j[i] : j[i] == 0); --r) d_out_seg[r] = pos[i];
         }
     }
     if (probe_row) {
@@ -492,7 +511,7 @@ probe_emit_kernel(TableView t, int32_t S, const int64_t* __restrict__ fk, const 
 #pragma unroll
     for (int i = 0; i < kItems; ++i) {
         if (mr[i] >= kNoMatch) continue;
-        const int q = segq[i];
+        const int q = S > 1 ? seg_of(pseg, S, j[i]) : 0;
         const int64_t t0 = t.seg[q], t1 = t.seg[q + 1];
         const int64_t sb = 2 * t0 + 2 * static_cast<int64_t>(q);
         const uint32_t cap = static_cast<uint32_t>(2 * (t1 - t0) + 2);

@@ -332,6 +332,29 @@ def test_groupby_dense_segmented_hot_partition(px):
     assert_groups_equal(res, want, 1, segmented=True)
 
 
+@pytest.mark.parametrize("n", [200_000, 1_500_000])
+def test_groupby_dense_global_direct_and_block(px, n):
+    # max_groups covers the whole (segment, key) space, so results go to the dense
+    # global array: 200K rows add into it row by row (too few rows to give each of
+    # the 152 SMs a block that amortises its block arrays); 1.5M rows use block
+    # arrays flushed per segment. Zipf-skewed keys from the at-scale shape.
+    d = pxdata.plain_at_scale(20_000, n, nattr=700)
+    pr, br, _ = oracle.join(d["pk"], d["fk"])
+    attr, amount = d["attr"][br], d["amount"][pr]
+    seg = np.array([0, n // 7, n // 7, n // 2, n - 3, n], np.int64)
+    want = oracle.groupby([attr], [(oracle.SUM, amount, None), (oracle.COUNT, None, None)], seg=seg)
+    res = _gb(px, [attr, amount], [0], [(px.PX_SUM, 1, None), (px.PX_COUNT, None, None)], 5 * 700,
+              seg=dev(seg), key_range=[(0, 699)])
+    assert_groups_equal(res, want, 1, segmented=True)
+    # without COUNT (occupancy bitmap) and a key outside the range (global path)
+    attr2 = attr.copy()
+    attr2[::9973] = 5000
+    want = oracle.groupby([attr2], [(oracle.SUM, amount, None)], seg=seg)
+    res = _gb(px, [attr2, amount], [0], [(px.PX_SUM, 1, None)], 5 * 700 + 64, seg=dev(seg),
+              key_range=[(0, 699)])
+    assert_groups_equal(res, want, 1, segmented=True)
+
+
 def test_groupby_capacity_overflow_reported(px):
     k = np.arange(1000, dtype=np.int32)
     ws = px.Workspace(1 << 20)
