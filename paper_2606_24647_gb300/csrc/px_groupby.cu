@@ -28,9 +28,9 @@
 namespace px {
 namespace {
 
-constexpr int kThreads = 512;
+constexpr int kThreads = 1024;
 constexpr int kWarps = kThreads / 32;
-constexpr int kItems = 8;
+constexpr int kItems = 4;
 constexpr int kTile = kThreads * kItems;
 constexpr int kSmemProbes = 8;
 constexpr int kMajority = 6;  // smallest group worth a warp reduction

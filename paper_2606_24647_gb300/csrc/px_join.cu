@@ -5,13 +5,17 @@
 // Table (caller memory, private layout):
 //   [0, 64)            header: magic, nsegs, unique flag
 //   [64, 64 + A)       copy of the build segment offsets (nsegs + 1 int64)
-//   [64 + A, ...)      slots of 16 bytes {int64 key, int32 build row, int32 pad}
-// Segment q of n_q rows owns 2 n_q + 2 slots starting at slot 2 seg[q] + 2 q, so
-// every segment runs at load factor <= 1/2 and the whole table is exactly
-// 2 n + 2 nsegs slots with no size known before the build. A key's home slot is
-// the multiply-shift reduction of the LOWER 32 bits of fmix64(key) (the exchange
-// uses the upper 32) onto the segment's slot pairs, i.e. an even slot, then linear
-// probing. Empty slots hold INT64_MIN.
+//   [64 + A, ...)      buckets of 64 bytes: 4 int64 keys, their 4 int32 build
+//                      rows, 16 bytes of padding
+// Segment q of n_q rows owns buckets [b_q, b_{q+1}) with b_q = floor(seg[q] / 2) + q,
+// i.e. at least (n_q + 1) / 2 buckets = 2 n_q + 2 slots, so every segment runs at
+// load factor < 1/2 and the whole table is floor(n / 2) + nsegs buckets with no
+// size known before the build. Slots are numbered 4 * bucket + lane. Linear
+// probing over slots starts at the first slot of the key's home bucket: the
+// multiply-shift reduction of the LOWER 32 bits of fmix64(key) (the exchange uses
+// the upper 32) onto the segment's buckets. The 4 keys of a bucket share one
+// aligned 32-byte sector, so the first 4 probes cost one sector read. Empty slots
+// hold the key INT64_MIN.
 #include <algorithm>
 
 #include "px_common.cuh"
@@ -20,7 +24,7 @@ namespace px {
 namespace {
 
 constexpr int64_t kEmpty = INT64_MIN;
-constexpr int64_t kMagic = 0x707874626c763031ll;  // "pxtblv01"
+constexpr int64_t kMagic = 0x707874626c763032ll;  // "pxtblv02"
 
 struct TableHeader {
     int64_t magic;
@@ -30,18 +34,20 @@ struct TableHeader {
     int64_t reserved[5];
 };
 
-struct Slot {
-    int64_t key;
-    int32_t row;
-    int32_t pad;
+struct Bucket {
+    int64_t key[4];
+    int32_t row[4];
+    int32_t pad[4];
 };
+static_assert(sizeof(Bucket) == 64, "bucket is one half of a 128-byte line");
 
 size_t seg_area_bytes(int32_t S) { return align_up(static_cast<size_t>(S + 1) * 8, 64); }
+__host__ __device__ inline int64_t table_buckets(int64_t n, int32_t S) { return n / 2 + S; }
 
 struct TableView {
     TableHeader* hdr;
     int64_t* seg;
-    Slot* slots;
+    Bucket* bk;
 };
 
 TableView table_view(void* d_table, int32_t S) {
@@ -49,16 +55,24 @@ TableView table_view(void* d_table, int32_t S) {
     char* b = static_cast<char*>(d_table);
     t.hdr = reinterpret_cast<TableHeader*>(b);
     t.seg = reinterpret_cast<int64_t*>(b + 64);
-    t.slots = reinterpret_cast<Slot*>(b + 64 + seg_area_bytes(S));
+    t.bk = reinterpret_cast<Bucket*>(b + 64 + seg_area_bytes(S));
     return t;
 }
 
-// Home slot of a key in a segment of `cap` slots (cap is even, segment bases are
-// even and the slot array is 64-byte aligned): an even slot, so the home slot and
-// its successor - the first two probes - share one aligned 32-byte sector.
-__device__ __forceinline__ uint32_t home_slot(uint64_t key, uint32_t cap) {
-    return 2 * slot_of(fmix64(key), cap / 2);
+// Buckets of segment q: [b0, b0 + nb).
+struct SegGeom {
+    int64_t b0;
+    uint32_t nb;
+};
+__device__ __forceinline__ SegGeom seg_geom(const TableView& t, int q) {
+    const int64_t s0 = t.seg[q], s1 = t.seg[q + 1];
+    SegGeom g;
+    g.b0 = s0 / 2 + q;
+    g.nb = static_cast<uint32_t>(s1 / 2 - s0 / 2 + 1);
+    return g;
 }
+
+__device__ __forceinline__ uint32_t home_bucket(uint64_t key, uint32_t nb) { return slot_of(fmix64(key), nb); }
 
 // ------------------------------------------------------------------ build ----
 
@@ -73,7 +87,7 @@ __global__ void build_init_kernel(TableView t, int32_t S, int32_t unique, const 
         t.hdr->unique = unique;
         t.hdr->nbuild = n;
         // Segment offsets clamped to be non-decreasing within [0, n] and to end at
-        // n, so no segment can address a slot outside the table.
+        // n, so no segment can address a bucket outside the table.
         int64_t prev = 0;
         t.seg[0] = 0;
         for (int q = 1; q < S; ++q) {
@@ -84,9 +98,10 @@ __global__ void build_init_kernel(TableView t, int32_t S, int32_t unique, const 
         }
         t.seg[S] = n;
     }
-    const int64_t nslots = 2 * n + 2 * static_cast<int64_t>(S);
-    longlong2* s2 = reinterpret_cast<longlong2*>(t.slots);
-    for (int64_t s = gtid; s < nslots; s += stride) s2[s] = make_longlong2(kEmpty, 0xffffffffll);
+    // Keys of every bucket to empty (16-byte stores; rows are written on insert).
+    const int64_t nwords = 2 * table_buckets(n, S);
+    for (int64_t w = gtid; w < nwords; w += stride)
+        reinterpret_cast<longlong2*>(&t.bk[w >> 1].key[2 * (w & 1)])[0] = make_longlong2(kEmpty, kEmpty);
 }
 
 __global__ void build_insert_kernel(TableView t, int32_t S, int32_t unique, const int64_t* __restrict__ pk,
@@ -100,24 +115,24 @@ __global__ void build_insert_kernel(TableView t, int32_t S, int32_t unique, cons
         return;
     }
     const int q = S > 1 ? seg_of(t.seg, S, i) : 0;
-    const int64_t s0 = t.seg[q], s1 = t.seg[q + 1];
-    const int64_t base = 2 * s0 + 2 * static_cast<int64_t>(q);
-    const uint32_t cap = static_cast<uint32_t>(2 * (s1 - s0) + 2);
-    uint32_t s = home_slot(static_cast<uint64_t>(key), cap);
-    for (uint32_t probe = 0; probe < cap; ++probe) {
-        Slot* slot = &t.slots[base + s];
-        const unsigned long long prev = atomicCAS(reinterpret_cast<unsigned long long*>(&slot->key),
+    const SegGeom g = seg_geom(t, q);
+    Bucket* bk = t.bk + g.b0;
+    const uint64_t nslots = 4ull * g.nb;
+    uint64_t s = 4ull * home_bucket(static_cast<uint64_t>(key), g.nb);
+    for (uint64_t probe = 0; probe < nslots; ++probe) {
+        Bucket& b = bk[s >> 2];
+        const unsigned long long prev = atomicCAS(reinterpret_cast<unsigned long long*>(&b.key[s & 3]),
                                                   static_cast<unsigned long long>(kEmpty),
                                                   static_cast<unsigned long long>(key));
         if (prev == static_cast<unsigned long long>(kEmpty)) {
-            slot->row = static_cast<int32_t>(i);
+            b.row[s & 3] = static_cast<int32_t>(i);
             return;
         }
         if (unique && prev == static_cast<unsigned long long>(key)) {
             set_status(status, PX_ERR_DUPLICATE_KEY);
             return;
         }
-        if (++s == cap) s = 0;
+        if (++s == nslots) s = 0;
     }
     set_status(status, PX_ERR_TABLE_FULL);
 }
@@ -192,20 +207,22 @@ __device__ __forceinline__ int64_t tile_pos(int64_t tile, int warp, int i, int l
     return tile * kTile + warp * (32 * kItems) + i * 32 + lane;
 }
 
-// Number of matches of `key` along the probe sequence from `s` in one segment's
-// slots, and the slot of the first one.
-__device__ __forceinline__ int32_t count_matches(const Slot* seg_slots, uint32_t cap, uint32_t s, int64_t key,
+// Number of matches of `key` along the probe sequence from slot `s` (numbered
+// within the segment's buckets), and the slot of the first one. Multi-map tables
+// hold fewer than 2^30 rows, so segment slot numbers fit 32 bits.
+__device__ __forceinline__ int32_t count_matches(const Bucket* segb, uint32_t nb, uint32_t s, int64_t key,
                                                  uint32_t* first) {
+    const uint32_t nslots = 4 * nb;
     int32_t m = 0;
-    for (uint32_t probe = 0; probe < cap; ++probe) {
-        const longlong2 v = *reinterpret_cast<const longlong2*>(&seg_slots[s]);
-        if (v.x == key) {
+    for (uint32_t probe = 0; probe < nslots; ++probe) {
+        const int64_t k = segb[s >> 2].key[s & 3];
+        if (k == key) {
             if (m == 0) *first = s;
             ++m;
-        } else if (v.x == kEmpty) {
+        } else if (k == kEmpty) {
             break;
         }
-        if (++s == cap) s = 0;
+        if (++s == nslots) s = 0;
     }
     return m;
 }
@@ -224,25 +241,18 @@ __device__ __forceinline__ void match_keys(const int64_t* __restrict__ fk, const
 }
 
 // Segment cursor of one thread: segment q holds the thread's latest position,
-// `end` is where q's positions end, sb/cap locate q's table slots. A thread's
-// positions only increase, so the cursor only moves forward.
+// `end` is where q's positions end, g locates q's buckets. A thread's positions
+// only increase, so the cursor only moves forward.
 struct SegCursor {
     int q;
     int64_t end;
-    int64_t sb;
-    uint32_t cap;
+    SegGeom g;
 };
-
-__device__ __forceinline__ void cursor_table(SegCursor& c, const TableView& t) {
-    const int64_t t0 = t.seg[c.q], t1 = t.seg[c.q + 1];
-    c.sb = 2 * t0 + 2 * static_cast<int64_t>(c.q);
-    c.cap = static_cast<uint32_t>(2 * (t1 - t0) + 2);
-}
 
 __device__ __forceinline__ void cursor_init(SegCursor& c, const TableView& t, const int64_t* pseg, int S, int64_t j) {
     c.q = S > 1 ? seg_of(pseg, S, j) : 0;
     c.end = c.q + 1 < S ? pseg[c.q + 1] : INT64_MAX;
-    cursor_table(c, t);
+    c.g = seg_geom(t, c.q);
 }
 
 __device__ __forceinline__ void cursor_seek(SegCursor& c, const TableView& t, const int64_t* pseg, int S, int64_t j) {
@@ -251,14 +261,69 @@ __device__ __forceinline__ void cursor_seek(SegCursor& c, const TableView& t, co
         ++c.q;
         c.end = c.q + 1 < S ? pseg[c.q + 1] : INT64_MAX;
     } while (j >= c.end);
-    cursor_table(c, t);
+    c.g = seg_geom(t, c.q);
+}
+
+// Looks `key` up in the 4 keys k01, k23 of one bucket: the lane of the match, or
+// -1 with *end set when an empty slot ends the probe sequence in this bucket.
+__device__ __forceinline__ int bucket_find(longlong2 k01, longlong2 k23, int64_t key, bool* end) {
+    *end = false;
+    if (k01.x == key) return 0;
+    if (k01.x == kEmpty) { *end = true; return -1; }
+    if (k01.y == key) return 1;
+    if (k01.y == kEmpty) { *end = true; return -1; }
+    if (k23.x == key) return 2;
+    if (k23.x == kEmpty) { *end = true; return -1; }
+    if (k23.y == key) return 3;
+    if (k23.y == kEmpty) { *end = true; return -1; }
+    return -1;
+}
+
+constexpr int kMatchWarps = kMatchThreads / 32;
+constexpr int kDeferCap = 32 + 32 * kMatchItems;  // fewer than 32 left over plus one tile's items
+
+// A lookup whose home bucket was full without its key, queued per warp so that
+// the rare walk on runs 32 keys at a time instead of stalling whole warps.
+struct Deferred {
+    int64_t j;        // probe position
+    int64_t key;
+    const Bucket* b;  // bucket read last
+    int32_t q;        // table segment
+    int32_t pad;
+};
+
+// Walks on from bucket e.b through the rest of its segment; records the build row
+// (or kNoMatch) of position e.j and counts a match in its tile.
+__device__ __forceinline__ void resolve_deferred(const TableView& t, const Deferred& e, int32_t* mrow,
+                                                 int32_t* tile_cnt) {
+    const SegGeom g = seg_geom(t, e.q);
+    const Bucket* segb = t.bk + g.b0;
+    const Bucket* b = e.b;
+    int32_t r = kNoMatch;
+    for (uint32_t round = 1; round < g.nb; ++round) {
+        b = b + 1 == segb + g.nb ? segb : b + 1;
+        const longlong2 k01 = *reinterpret_cast<const longlong2*>(&b->key[0]);
+        const longlong2 k23 = *reinterpret_cast<const longlong2*>(&b->key[2]);
+        bool end;
+        const int l = bucket_find(k01, k23, e.key, &end);
+        if (l >= 0) {
+            r = b->row[l];
+            break;
+        }
+        if (end) break;
+    }
+    mrow[e.j] = r;
+    if (r != kNoMatch) atomicAdd(&tile_cnt[e.j / kTile], 1);
 }
 
 // Persistent over tiles (grid-stride), software-pipelined: the next tile's keys
-// are loaded while the current tile's table slots are in flight. No block-wide
+// are loaded while the current tile's buckets are in flight. No block-wide
 // barrier: every thread reads the (cached) table header once and follows its own
-// segment cursor; warps add their match counts atomically.
-__global__ void __launch_bounds__(kMatchThreads, 4)
+// segment cursor; warps add their match counts atomically. Unique tables: every
+// position reads its home bucket's 4 keys (one sector), then the build row of a
+// match; the few keys whose bucket is full without them go to the warp's queue,
+// drained 32 at a time (and once more at the end).
+__global__ void __launch_bounds__(kMatchThreads, 3)
 probe_match_kernel(TableView t, int32_t S, const int64_t* __restrict__ fk, const int32_t* __restrict__ sel,
                    const int64_t* __restrict__ d_n, int64_t ncap, const int64_t* __restrict__ pseg,
                    int32_t* __restrict__ mrow, int32_t* __restrict__ tile_cnt, int32_t* status, int32_t npay,
@@ -270,8 +335,20 @@ probe_match_kernel(TableView t, int32_t S, const int64_t* __restrict__ fk, const
     const bool unique = t.hdr->unique != 0;
     const int64_t lane_off = warp * (32 * kMatchItems) + lane;  // item i of a tile at tile * kTile + lane_off + 32 i
     int64_t tile = blockIdx.x;
+    if (bad) {  // a table this call cannot use: no matches, and no reads past its header
+        for (; tile < ntiles; tile += gridDim.x)
+#pragma unroll
+            for (int i = 0; i < kMatchItems; ++i) {
+                const int64_t j = tile * kTile + lane_off + 32 * i;
+                if (j < ncap) mrow[j] = kNoMatch;
+            }
+        return;
+    }
     if (tile >= ntiles) return;
-    const int64_t nv = bad ? 0 : n;  // positions with a key to look up
+    __shared__ Deferred s_def[kMatchWarps][kDeferCap];
+    Deferred* const dq = s_def[warp];
+    uint32_t nq = 0;  // entries in this warp's queue (warp-uniform)
+    const int64_t nv = n;  // positions with a key to look up
     SegCursor c;
     cursor_init(c, t, pseg, S, tile * kTile + lane_off);
     int64_t keyv[kMatchItems];
@@ -279,82 +356,79 @@ probe_match_kernel(TableView t, int32_t S, const int64_t* __restrict__ fk, const
     for (; tile < ntiles; tile += gridDim.x) {
         const int64_t j0 = tile * kTile + lane_off;
         int32_t out[kMatchItems];
+        uint32_t defer = 0;  // items queued for the walk on
         int segq[kMatchItems];
-        const Slot* pair[kMatchItems];
+        uint32_t hb[kMatchItems];  // home bucket, numbered within the segment
+        const Bucket* bp[kMatchItems];
 #pragma unroll
         for (int i = 0; i < kMatchItems; ++i) {
             cursor_seek(c, t, pseg, S, j0 + 32 * i);
             segq[i] = c.q;
-            pair[i] = t.slots + c.sb + home_slot(static_cast<uint64_t>(keyv[i]), c.cap);
+            hb[i] = home_bucket(static_cast<uint64_t>(keyv[i]), c.g.nb);
+            bp[i] = t.bk + c.g.b0 + hb[i];
             out[i] = kNoMatch;
         }
         if (unique) {
-            longlong2 v0[kMatchItems], v1[kMatchItems];
+            longlong2 k01[kMatchItems], k23[kMatchItems];
 #pragma unroll
             for (int i = 0; i < kMatchItems; ++i) {
                 if (keyv[i] != kEmpty) {
-                    v0[i] = *reinterpret_cast<const longlong2*>(pair[i]);
-                    v1[i] = *reinterpret_cast<const longlong2*>(pair[i] + 1);
+                    k01[i] = *reinterpret_cast<const longlong2*>(&bp[i]->key[0]);
+                    k23[i] = *reinterpret_cast<const longlong2*>(&bp[i]->key[2]);
                 } else {
-                    v0[i] = v1[i] = make_longlong2(kEmpty, 0);
+                    k01[i] = k23[i] = make_longlong2(kEmpty, kEmpty);
                 }
             }
-            // Next tile's keys go out while this tile's slots are in flight.
+            // Next tile's keys go out while this tile's buckets are in flight.
             int64_t keyn[kMatchItems];
             match_keys(fk, sel, nv, (tile + gridDim.x) * kTile + lane_off, keyn);
-            uint32_t hits = 0;
 #pragma unroll
             for (int i = 0; i < kMatchItems; ++i) {
-                const int64_t key = keyv[i];
-                if (key == kEmpty) continue;
-                if (v0[i].x == key) {
-                    out[i] = static_cast<int32_t>(v0[i].y);
-                } else if (v0[i].x != kEmpty) {
-                    if (v1[i].x == key) {
-                        out[i] = static_cast<int32_t>(v1[i].y);
-                    } else if (v1[i].x != kEmpty) {
-                        // Rare: continue linear probing past the pair within the segment.
-                        const int q = segq[i];
-                        const int64_t t0 = t.seg[q], t1 = t.seg[q + 1];
-                        const Slot* seg_slots = t.slots + 2 * t0 + 2 * static_cast<int64_t>(q);
-                        const uint32_t cap = static_cast<uint32_t>(2 * (t1 - t0) + 2);
-                        uint32_t s = static_cast<uint32_t>(pair[i] - seg_slots) + 2;
-                        if (s >= cap) s -= cap;
-                        for (uint32_t probe = 2; probe < cap; ++probe) {
-                            const longlong2 w = *reinterpret_cast<const longlong2*>(&seg_slots[s]);
-                            if (w.x == key) {
-                                out[i] = static_cast<int32_t>(w.y);
-                                break;
-                            }
-                            if (w.x == kEmpty) break;
-                            if (++s == cap) s = 0;
-                        }
-                    }
+                bool end;
+                const int l = bucket_find(k01[i], k23[i], keyv[i], &end);
+                const bool valid = keyv[i] != kEmpty;
+                if (valid && l >= 0) out[i] = bp[i]->row[l];
+                const bool d = valid && l < 0 && !end;
+                const uint32_t dm = __ballot_sync(FULL, d);
+                if (d) {
+                    Deferred& e = dq[nq + __popc(dm & lanemask_lt())];
+                    e.j = j0 + 32 * i;
+                    e.key = keyv[i];
+                    e.b = bp[i];
+                    e.q = segq[i];
+                    defer |= 1u << i;
                 }
+                nq += __popc(dm);
             }
+            uint32_t hits = 0;
 #pragma unroll
             for (int i = 0; i < kMatchItems; ++i) {
                 hits += __popc(__ballot_sync(FULL, out[i] != kNoMatch));
                 keyv[i] = keyn[i];
             }
             if (lane == 0 && hits) atomicAdd(&tile_cnt[tile], static_cast<int32_t>(hits));  // zeroed before launch
+            if (nq >= 32) {
+                __syncwarp();
+                do {
+                    const Deferred e = dq[nq - 32 + lane];
+                    __syncwarp();
+                    resolve_deferred(t, e, mrow, tile_cnt);
+                    nq -= 32;
+                } while (nq >= 32);
+            }
         } else {
             // Multi-map: count every match; one match is recorded as its build row,
-            // several as -(global slot of the first + 2) for the emit pass to walk.
+            // several as -(table slot of the first + 2) for the emit pass to walk.
             int32_t cnt = 0;
 #pragma unroll
             for (int i = 0; i < kMatchItems; ++i) {
                 if (keyv[i] == kEmpty) continue;
-                const int q = segq[i];
-                const int64_t t0 = t.seg[q], t1 = t.seg[q + 1];
-                const int64_t sb = 2 * t0 + 2 * static_cast<int64_t>(q);
-                const Slot* seg_slots = t.slots + sb;
-                const uint32_t cap = static_cast<uint32_t>(2 * (t1 - t0) + 2);
+                const SegGeom g = seg_geom(t, segq[i]);
+                const Bucket* segb = t.bk + g.b0;
                 uint32_t first = 0;
-                const int32_t m =
-                    count_matches(seg_slots, cap, static_cast<uint32_t>(pair[i] - seg_slots), keyv[i], &first);
-                if (m == 1) out[i] = seg_slots[first].row;
-                else if (m > 1) out[i] = -static_cast<int32_t>(sb + first) - 2;
+                const int32_t m = count_matches(segb, g.nb, 4 * hb[i], keyv[i], &first);
+                if (m == 1) out[i] = segb[first >> 2].row[first & 3];
+                else if (m > 1) out[i] = -static_cast<int32_t>(4 * g.b0 + first) - 2;
                 cnt += m;
             }
             match_keys(fk, sel, nv, (tile + gridDim.x) * kTile + lane_off, keyv);
@@ -364,9 +438,11 @@ probe_match_kernel(TableView t, int32_t S, const int64_t* __restrict__ fk, const
 #pragma unroll
         for (int i = 0; i < kMatchItems; ++i) {
             const int64_t j = j0 + 32 * i;
-            if (j < ncap) mrow[j] = out[i];
+            if (j < ncap && !((defer >> i) & 1u)) mrow[j] = out[i];
         }
     }
+    __syncwarp();
+    if (lane < static_cast<int>(nq)) resolve_deferred(t, dq[lane], mrow, tile_cnt);
 }
 
 constexpr int kScanThreads = 256;
@@ -446,14 +522,11 @@ probe_emit_kernel(TableView t, int32_t S, const int64_t* __restrict__ fk, const 
         m[i] = mr[i] >= 0 ? 1 : 0;
         key[i] = 0;
         if (mr[i] >= kNoMatch) continue;
-        const int q = S > 1 ? seg_of(pseg, S, j[i]) : 0;
-        const int64_t t0 = t.seg[q], t1 = t.seg[q + 1];
-        const int64_t sb = 2 * t0 + 2 * static_cast<int64_t>(q);
-        const uint32_t cap = static_cast<uint32_t>(2 * (t1 - t0) + 2);
-        const uint32_t first = static_cast<uint32_t>(-static_cast<int64_t>(mr[i]) - 2 - sb);
+        const SegGeom g = seg_geom(t, S > 1 ? seg_of(pseg, S, j[i]) : 0);
+        const uint32_t first = static_cast<uint32_t>(-static_cast<int64_t>(mr[i]) - 2 - 4 * g.b0);
         key[i] = fk[prow[i]];
         uint32_t dummy = 0;
-        m[i] = count_matches(t.slots + sb, cap, first, key[i], &dummy);
+        m[i] = count_matches(t.bk + g.b0, g.nb, first, key[i], &dummy);
     }
     // Output rows in position order (warp, item, lane): warp scans, then a block
     // combine; the tile's first row comes from the scan of the tile counts.
@@ -511,21 +584,20 @@ probe_emit_kernel(TableView t, int32_t S, const int64_t* __restrict__ fk, const 
 #pragma unroll
     for (int i = 0; i < kItems; ++i) {
         if (mr[i] >= kNoMatch) continue;
-        const int q = S > 1 ? seg_of(pseg, S, j[i]) : 0;
-        const int64_t t0 = t.seg[q], t1 = t.seg[q + 1];
-        const int64_t sb = 2 * t0 + 2 * static_cast<int64_t>(q);
-        const uint32_t cap = static_cast<uint32_t>(2 * (t1 - t0) + 2);
-        uint32_t s = static_cast<uint32_t>(-static_cast<int64_t>(mr[i]) - 2 - sb);
+        const SegGeom g = seg_geom(t, S > 1 ? seg_of(pseg, S, j[i]) : 0);
+        const Bucket* segb = t.bk + g.b0;
+        const uint32_t nslots = 4 * g.nb;
+        uint32_t s = static_cast<uint32_t>(-static_cast<int64_t>(mr[i]) - 2 - 4 * g.b0);
         int64_t p = pos[i];
-        for (uint32_t probe = 0; probe < cap && p < pos[i] + m[i]; ++probe) {
-            const longlong2 v = *reinterpret_cast<const longlong2*>(&t.slots[sb + s]);
-            if (v.x == key[i]) {
-                if (p < out_cap) emit(oc, p, prow[i], static_cast<int32_t>(v.y), probe_row, build_row);
+        for (uint32_t probe = 0; probe < nslots && p < pos[i] + m[i]; ++probe) {
+            const int64_t k = segb[s >> 2].key[s & 3];
+            if (k == key[i]) {
+                if (p < out_cap) emit(oc, p, prow[i], segb[s >> 2].row[s & 3], probe_row, build_row);
                 ++p;
-            } else if (v.x == kEmpty) {
+            } else if (k == kEmpty) {
                 break;
             }
-            if (++s == cap) s = 0;
+            if (++s == nslots) s = 0;
         }
     }
 }
@@ -571,7 +643,7 @@ extern "C" {
 size_t px_join_table_bytes(int64_t nbuild, int32_t nsegs) {
     if (nbuild < 0) nbuild = 0;
     const int32_t S = nsegs > 0 ? nsegs : 1;
-    return 64 + seg_area_bytes(S) + (2 * static_cast<size_t>(nbuild) + 2 * static_cast<size_t>(S)) * sizeof(Slot);
+    return 64 + seg_area_bytes(S) + static_cast<size_t>(table_buckets(nbuild, S)) * sizeof(Bucket);
 }
 
 size_t px_join_build_ws_bytes(int64_t nbuild) {
@@ -598,17 +670,17 @@ px_status px_join_build(const px_batch* build, int32_t pk_col, const int64_t* d_
     if (table_bytes < px_join_table_bytes(build->nrows, nsegs))
         return fail(PX_ERR_INVALID, "px_join_build: table of %zu bytes, %zu needed", table_bytes,
                     px_join_table_bytes(build->nrows, nsegs));
-    if (!unique && build->nrows >= (int64_t(1) << 30))
-        return fail(PX_ERR_UNSUPPORTED, "px_join_build: multi-map tables hold below 2^30 rows");
+    if (!unique && 4 * table_buckets(build->nrows, nsegs > 0 ? nsegs : 1) + 2 > INT32_MAX)
+        return fail(PX_ERR_UNSUPPORTED, "px_join_build: multi-map tables hold below about 2^30 rows");
     s = check_ws(d_ws, ws_bytes, px_join_build_ws_bytes(build->nrows), "px_join_build");
     if (s != PX_OK) return s;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const int32_t S = nsegs > 0 ? nsegs : 1;
     const TableView t = table_view(d_table, S);
     const int64_t ncap = build->nrows;
-    const int64_t nslots = 2 * ncap + 2 * S;
+    const int64_t nwords = 2 * table_buckets(ncap, S);  // 16-byte key words to clear
     const int threads = 256;
-    const unsigned init_blocks = static_cast<unsigned>(std::min<int64_t>(cdiv(nslots, threads), 8192));
+    const unsigned init_blocks = static_cast<unsigned>(std::min<int64_t>(cdiv(nwords, threads), 8192));
     build_init_kernel<<<init_blocks, threads, 0, st>>>(t, S, unique ? 1 : 0, d_seg, build->d_nrows, ncap);
     note_launch();
     if ((s = check_launch("px_join_build init")) != PX_OK) return s;
