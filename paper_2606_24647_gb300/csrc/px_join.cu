@@ -227,15 +227,15 @@ __device__ __forceinline__ int32_t count_matches(const Bucket* segb, uint32_t nb
     return m;
 }
 
-constexpr int kMatchThreads = 256;
-constexpr int kMatchItems = kTile / kMatchThreads;  // 4 positions per thread per tile, same tile as emit
+constexpr int kMatchThreads = 512;
+constexpr int kMatchItems = kTile / kMatchThreads;  // positions per thread per tile (same tiles as emit)
 
 // Keys of this thread's positions of tile `tile` (kEmpty where there is no row).
 __device__ __forceinline__ void match_keys(const int64_t* __restrict__ fk, const int32_t* __restrict__ sel,
-                                           int64_t n, int64_t j0, int64_t* keyv) {
+                                           uint32_t n, uint32_t j0, int64_t* keyv) {
 #pragma unroll
     for (int i = 0; i < kMatchItems; ++i) {
-        const int64_t j = j0 + 32 * i;
+        const uint32_t j = j0 + 32 * i;
         keyv[i] = j < n ? fk[sel ? static_cast<int64_t>(sel[j]) : j] : kEmpty;
     }
 }
@@ -323,7 +323,7 @@ __device__ __forceinline__ void resolve_deferred(const TableView& t, const Defer
 // position reads its home bucket's 4 keys (one sector), then the build row of a
 // match; the few keys whose bucket is full without them go to the warp's queue,
 // drained 32 at a time (and once more at the end).
-__global__ void __launch_bounds__(kMatchThreads, 3)
+__global__ void __launch_bounds__(kMatchThreads, 2)
 probe_match_kernel(TableView t, int32_t S, const int64_t* __restrict__ fk, const int32_t* __restrict__ sel,
                    const int64_t* __restrict__ d_n, int64_t ncap, const int64_t* __restrict__ pseg,
                    int32_t* __restrict__ mrow, int32_t* __restrict__ tile_cnt, int32_t* status, int32_t npay,
@@ -333,7 +333,9 @@ probe_match_kernel(TableView t, int32_t S, const int64_t* __restrict__ fk, const
     const bool bad = t.hdr->magic != kMagic || t.hdr->nsegs != S || (npay > 0 && t.hdr->nbuild > payload_rows);
     if (bad && blockIdx.x == 0 && threadIdx.x == 0) set_status(status, PX_ERR_INVALID);
     const bool unique = t.hdr->unique != 0;
-    const int64_t lane_off = warp * (32 * kMatchItems) + lane;  // item i of a tile at tile * kTile + lane_off + 32 i
+    // Positions fit 32 bits (batches hold at most INT32_MAX rows); item i of a tile
+    // sits at tile * kTile + lane_off + 32 i.
+    const uint32_t lane_off = warp * (32 * kMatchItems) + lane;
     int64_t tile = blockIdx.x;
     if (bad) {  // a table this call cannot use: no matches, and no reads past its header
         for (; tile < ntiles; tile += gridDim.x)
@@ -348,13 +350,13 @@ probe_match_kernel(TableView t, int32_t S, const int64_t* __restrict__ fk, const
     __shared__ Deferred s_def[kMatchWarps][kDeferCap];
     Deferred* const dq = s_def[warp];
     uint32_t nq = 0;  // entries in this warp's queue (warp-uniform)
-    const int64_t nv = n;  // positions with a key to look up
+    const uint32_t nv = static_cast<uint32_t>(n);  // positions with a key to look up
     SegCursor c;
-    cursor_init(c, t, pseg, S, tile * kTile + lane_off);
+    cursor_init(c, t, pseg, S, static_cast<uint32_t>(tile) * kTile + lane_off);
     int64_t keyv[kMatchItems];
-    match_keys(fk, sel, nv, tile * kTile + lane_off, keyv);
+    match_keys(fk, sel, nv, static_cast<uint32_t>(tile) * kTile + lane_off, keyv);
     for (; tile < ntiles; tile += gridDim.x) {
-        const int64_t j0 = tile * kTile + lane_off;
+        const uint32_t j0 = static_cast<uint32_t>(tile) * kTile + lane_off;
         int32_t out[kMatchItems];
         uint32_t defer = 0;  // items queued for the walk on
         int segq[kMatchItems];
@@ -381,7 +383,7 @@ probe_match_kernel(TableView t, int32_t S, const int64_t* __restrict__ fk, const
             }
             // Next tile's keys go out while this tile's buckets are in flight.
             int64_t keyn[kMatchItems];
-            match_keys(fk, sel, nv, (tile + gridDim.x) * kTile + lane_off, keyn);
+            match_keys(fk, sel, nv, static_cast<uint32_t>(tile + gridDim.x) * kTile + lane_off, keyn);
 #pragma unroll
             for (int i = 0; i < kMatchItems; ++i) {
                 bool end;
@@ -431,13 +433,13 @@ probe_match_kernel(TableView t, int32_t S, const int64_t* __restrict__ fk, const
                 else if (m > 1) out[i] = -static_cast<int32_t>(4 * g.b0 + first) - 2;
                 cnt += m;
             }
-            match_keys(fk, sel, nv, (tile + gridDim.x) * kTile + lane_off, keyv);
+            match_keys(fk, sel, nv, static_cast<uint32_t>(tile + gridDim.x) * kTile + lane_off, keyv);
             cnt = warp_sum(cnt);
             if (lane == 0 && cnt) atomicAdd(&tile_cnt[tile], cnt);  // tile_cnt zeroed before the launch
         }
 #pragma unroll
         for (int i = 0; i < kMatchItems; ++i) {
-            const int64_t j = j0 + 32 * i;
+            const uint32_t j = j0 + 32 * i;
             if (j < ncap && !((defer >> i) & 1u)) mrow[j] = out[i];
         }
     }
@@ -500,49 +502,67 @@ probe_emit_kernel(TableView t, int32_t S, const int64_t* __restrict__ fk, const 
                   int64_t* __restrict__ d_out_seg) {
     __shared__ int32_t s_warp[kWarps];
     __shared__ int32_t s_q0;
-    const int64_t tile = blockIdx.x;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t n = actual_rows(d_n, ncap);
+    // Positions fit 32 bits (batches hold at most INT32_MAX rows).
+    const uint32_t tb = static_cast<uint32_t>(blockIdx.x) * kTile;
+    const int rows = n - tb >= kTile ? kTile : static_cast<int>(n - tb);  // valid positions in this tile (<= 0: none)
     // One thread finds the segment of the tile's first position for everyone.
-    if (d_out_seg && threadIdx.x == 0) s_q0 = (S > 1 && tile * kTile < n) ? seg_of(pseg, S, tile * kTile) : 0;
-    int64_t j[kItems];
-    int32_t mr[kItems], prow[kItems], m[kItems];
-    bool valid[kItems];
+    if (d_out_seg && threadIdx.x == 0) s_q0 = (S > 1 && rows > 0) ? seg_of(pseg, S, tb) : 0;
+    int lp[kItems];  // position within the tile
+    int32_t mr[kItems], prow[kItems];
 #pragma unroll
     for (int i = 0; i < kItems; ++i) {
-        j[i] = tile_pos(tile, warp, i, lane);
-        valid[i] = j[i] < n;
-        mr[i] = valid[i] ? mrow[j[i]] : kNoMatch;
-        prow[i] = valid[i] ? (sel ? sel[j[i]] : static_cast<int32_t>(j[i])) : 0;
+        lp[i] = warp * (32 * kItems) + i * 32 + lane;
+        const bool valid = lp[i] < rows;
+        mr[i] = valid ? mrow[tb + lp[i]] : kNoMatch;
+        prow[i] = valid ? (sel ? sel[tb + lp[i]] : static_cast<int32_t>(tb + lp[i])) : 0;
     }
-    // Matches per position: 1, 0, or (multi-map) counted again along the chain.
+    // Output rows in position order (warp, item, lane). Unique matches count 0 or 1,
+    // so a ballot per item ranks them; a warp holding a multi-map position (several
+    // matches, counted again along its chain) takes shuffle scans instead.
+    bool has_multi = false;
+#pragma unroll
+    for (int i = 0; i < kItems; ++i) has_multi |= mr[i] < kNoMatch;
+    const bool multi = __any_sync(FULL, has_multi);
+    int32_t m[kItems], pre[kItems];
     int64_t key[kItems];
-#pragma unroll
-    for (int i = 0; i < kItems; ++i) {
-        m[i] = mr[i] >= 0 ? 1 : 0;
-        key[i] = 0;
-        if (mr[i] >= kNoMatch) continue;
-        const SegGeom g = seg_geom(t, S > 1 ? seg_of(pseg, S, j[i]) : 0);
-        const uint32_t first = static_cast<uint32_t>(-static_cast<int64_t>(mr[i]) - 2 - 4 * g.b0);
-        key[i] = fk[prow[i]];
-        uint32_t dummy = 0;
-        m[i] = count_matches(t.bk + g.b0, g.nb, first, key[i], &dummy);
-    }
-    // Output rows in position order (warp, item, lane): warp scans, then a block
-    // combine; the tile's first row comes from the scan of the tile counts.
-    int32_t pre[kItems];
     int32_t wsum = 0;
+    if (!multi) {
+        const uint32_t lt = lanemask_lt();
 #pragma unroll
-    for (int i = 0; i < kItems; ++i) {
-        const int32_t incl = warp_incl_scan(m[i]);
-        pre[i] = wsum + incl - m[i];
-        wsum += __shfl_sync(FULL, incl, 31);
+        for (int i = 0; i < kItems; ++i) {
+            m[i] = mr[i] >= 0 ? 1 : 0;
+            key[i] = 0;
+            const uint32_t b = __ballot_sync(FULL, m[i] != 0);
+            pre[i] = wsum + __popc(b & lt);
+            wsum += __popc(b);
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < kItems; ++i) {
+            m[i] = mr[i] >= 0 ? 1 : 0;
+            key[i] = 0;
+            if (mr[i] < kNoMatch) {
+                const SegGeom g = seg_geom(t, S > 1 ? seg_of(pseg, S, tb + lp[i]) : 0);
+                const uint32_t first = static_cast<uint32_t>(-static_cast<int64_t>(mr[i]) - 2 - 4 * g.b0);
+                key[i] = fk[prow[i]];
+                uint32_t dummy = 0;
+                m[i] = count_matches(t.bk + g.b0, g.nb, first, key[i], &dummy);
+            }
+            const int32_t incl = warp_incl_scan(m[i]);
+            pre[i] = wsum + incl - m[i];
+            wsum += __shfl_sync(FULL, incl, 31);
+        }
     }
+    // Block combine; the tile's first row comes from the scan of the tile counts.
     if (lane == 0) s_warp[warp] = wsum;
     __syncthreads();
-    int32_t wbase = 0;
-    for (int w = 0; w < warp; ++w) wbase += s_warp[w];
-    const int64_t base = tile_off[tile] + wbase;
+    int32_t wb = lane < warp ? s_warp[lane] : 0;  // totals of the warps before this one, in lanes < kWarps
+#pragma unroll
+    for (int d = 1; d < kWarps; d <<= 1) wb += __shfl_xor_sync(FULL, wb, d);
+    wb = __shfl_sync(FULL, wb, 0);
+    const int64_t base = tile_off[blockIdx.x] + wb;
     int64_t pos[kItems];
     bool one[kItems];
 #pragma unroll
@@ -558,14 +578,15 @@ probe_emit_kernel(TableView t, int32_t S, const int64_t* __restrict__ fk, const 
         int64_t end = q + 1 < S ? pseg[q + 1] : INT64_MAX;
 #pragma unroll
         for (int i = 0; i < kItems; ++i) {
-            if (!valid[i]) continue;
-            while (j[i] >= end) {
+            if (lp[i] >= rows) continue;
+            const int64_t j = tb + lp[i];
+            while (j >= end) {
                 ++q;
                 start = end;
                 end = q + 1 < S ? pseg[q + 1] : INT64_MAX;
             }
-            if (j[i] == start)
-                for (int r = q; r >= 0 && (S > 1 ? pseg[r] == j[i] : j[i] == 0); --r) d_out_seg[r] = pos[i];
+            if (j == start)
+                for (int r = q; r >= 0 && (S > 1 ? pseg[r] == j : j == 0); --r) d_out_seg[r] = pos[i];
         }
     }
     if (probe_row) {
@@ -580,11 +601,12 @@ probe_emit_kernel(TableView t, int32_t S, const int64_t* __restrict__ fk, const 
     }
     for (int c = 0; c < oc.ncarry; ++c) gather_store(oc.carry_w[c], oc.carry_in[c], oc.carry_out[c], prow, pos, one);
     for (int c = 0; c < oc.npay; ++c) gather_store(oc.pay_w[c], oc.pay_in[c], oc.pay_out[c], mr, pos, one);
+    if (!multi) return;
     // Positions with several matches: walk the chain again, emitting each.
 #pragma unroll
     for (int i = 0; i < kItems; ++i) {
         if (mr[i] >= kNoMatch) continue;
-        const SegGeom g = seg_geom(t, S > 1 ? seg_of(pseg, S, j[i]) : 0);
+        const SegGeom g = seg_geom(t, S > 1 ? seg_of(pseg, S, tb + lp[i]) : 0);
         const Bucket* segb = t.bk + g.b0;
         const uint32_t nslots = 4 * g.nb;
         uint32_t s = static_cast<uint32_t>(-static_cast<int64_t>(mr[i]) - 2 - 4 * g.b0);
