@@ -201,12 +201,6 @@ __device__ __forceinline__ void emit(const OutCols& oc, int64_t pos, int64_t pro
     for (int c = 0; c < oc.npay; ++c) copy_cell(oc.pay_out[c], oc.pay_in[c], oc.pay_w[c], pos, brow);
 }
 
-// Position of item i of this thread in a tile: warp-contiguous runs of 32 * kItems,
-// lanes innermost, so position order = (warp, item, lane).
-__device__ __forceinline__ int64_t tile_pos(int64_t tile, int warp, int i, int lane) {
-    return tile * kTile + warp * (32 * kItems) + i * 32 + lane;
-}
-
 // Number of matches of `key` along the probe sequence from slot `s` (numbered
 // within the segment's buckets), and the slot of the first one. Multi-map tables
 // hold fewer than 2^30 rows, so segment slot numbers fit 32 bits.

@@ -39,6 +39,7 @@ struct Cols {
     const void* in[PX_MAX_COLS];
     void* out[PX_MAX_COLS];
     uint32_t stage_off[PX_MAX_COLS];  // byte offset of the column's tile in the staging area
+    int32_t order[PX_MAX_COLS];       // columns by decreasing width (the order they are moved in)
 };
 
 // Items per thread so that the staged tile of all columns fits kStageBudget.
@@ -133,15 +134,12 @@ part_scan_kernel(const int32_t* __restrict__ cnt, int32_t* __restrict__ offs, in
 }
 
 // Moves one column's tile from the staging area (tile order) into partition order
-// in shared memory, then writes each partition's run to its global position.
-// dest[k]: global output row of partition-ordered position threadIdx.x + k * kThreads
-// of the tile (-1 past the tile), computed once and reused by every column.
+// in buffer `buf` (shared memory).
 template <typename T, int ITEMS>
-__device__ __forceinline__ void scatter_col(const unsigned char* staged, void* sorted_raw, const int32_t* dest,
-                                            const int32_t* posv, const uint32_t* pidv, uint32_t nparts, void* out,
-                                            int warp, int lane) {
+__device__ __forceinline__ void transpose_col(const unsigned char* staged, unsigned char* buf, const int32_t* posv,
+                                              const uint32_t* pidv, uint32_t nparts, int warp, int lane) {
     const T* src = reinterpret_cast<const T*>(staged);
-    T* sorted = static_cast<T*>(sorted_raw);
+    T* sorted = reinterpret_cast<T*>(buf);
     T v[ITEMS];
 #pragma unroll
     for (int i = 0; i < ITEMS; ++i)
@@ -149,12 +147,18 @@ __device__ __forceinline__ void scatter_col(const unsigned char* staged, void* s
 #pragma unroll
     for (int i = 0; i < ITEMS; ++i)
         if (pidv[i] < nparts) sorted[posv[i]] = v[i];
-    __syncthreads();
+}
+
+// Writes a partition-ordered column tile to its global rows: dest[k] is the output
+// row of partition-ordered position threadIdx.x + k * kThreads (-1 past the tile),
+// so each partition's run is written contiguously.
+template <typename T, int ITEMS>
+__device__ __forceinline__ void store_col(const unsigned char* buf, const int32_t* dest, void* out) {
+    const T* sorted = reinterpret_cast<const T*>(buf);
     T* o = static_cast<T*>(out);
 #pragma unroll
     for (int k = 0; k < ITEMS; ++k)
         if (dest[k] >= 0) o[dest[k]] = sorted[threadIdx.x + k * kThreads];
-    __syncthreads();
 }
 
 template <typename T, int ITEMS>
@@ -291,19 +295,33 @@ part_scatter_kernel(Cols cols, int32_t key_col, const int32_t* __restrict__ sel,
         dest[k] = jj < tile_rows ? s_delta[s_pid[jj]] + jj : -1;
     }
 
-    for (int c = 0; c < cols.ncols; ++c) {
-        const unsigned char* st = stage + cols.stage_off[c];
-        switch (cols.width[c]) {
-            case 8:
-                scatter_col<int64_t, ITEMS>(st, sorted, dest, posv, pidv, nparts, cols.out[c], warp, lane);
-                break;
-            case 4:
-                scatter_col<int32_t, ITEMS>(st, sorted, dest, posv, pidv, nparts, cols.out[c], warp, lane);
-                break;
-            default:
-                scatter_col<int8_t, ITEMS>(st, sorted, dest, posv, pidv, nparts, cols.out[c], warp, lane);
-                break;
+    // Column phases, one barrier each: phase k writes column order[k-1] to global
+    // memory from its partition-ordered buffer while moving column order[k] into
+    // partition order. The first column's buffer is the sorted area; column
+    // order[k]'s is the staging area of column order[k-1], free once that column
+    // was moved and at least as large (decreasing widths).
+    for (int k = 0; k <= cols.ncols; ++k) {
+        if (k > 0) {
+            const int c = cols.order[k - 1];
+            const unsigned char* buf =
+                k == 1 ? static_cast<const unsigned char*>(sorted) : stage + cols.stage_off[cols.order[k - 2]];
+            switch (cols.width[c]) {
+                case 8: store_col<int64_t, ITEMS>(buf, dest, cols.out[c]); break;
+                case 4: store_col<int32_t, ITEMS>(buf, dest, cols.out[c]); break;
+                default: store_col<int8_t, ITEMS>(buf, dest, cols.out[c]); break;
+            }
         }
+        if (k < cols.ncols) {
+            const int c = cols.order[k];
+            unsigned char* buf = k == 0 ? static_cast<unsigned char*>(sorted) : stage + cols.stage_off[cols.order[k - 1]];
+            const unsigned char* st = stage + cols.stage_off[c];
+            switch (cols.width[c]) {
+                case 8: transpose_col<int64_t, ITEMS>(st, buf, posv, pidv, nparts, warp, lane); break;
+                case 4: transpose_col<int32_t, ITEMS>(st, buf, posv, pidv, nparts, warp, lane); break;
+                default: transpose_col<int8_t, ITEMS>(st, buf, posv, pidv, nparts, warp, lane); break;
+            }
+        }
+        __syncthreads();
     }
 }
 
@@ -423,6 +441,12 @@ px_status px_partition(const px_batch* in, int32_t key_col, const int32_t* d_sel
         cols.out[c] = out->cols[c].data;
         row_bytes += static_cast<uint32_t>(in->cols[c].type);
     }
+    // Move order: decreasing width (stable), so each column's partition-ordered
+    // buffer can be the staging area of the column moved before it.
+    int n_ord = 0;
+    for (int w : {8, 4, 1})
+        for (int c = 0; c < in->ncols; ++c)
+            if (cols.width[c] == w) cols.order[n_ord++] = c;
     const int items = items_for(row_bytes);
     const int64_t T = static_cast<int64_t>(kThreads) * items;
     uint32_t stage_bytes = 0;
