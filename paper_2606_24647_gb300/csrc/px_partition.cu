@@ -28,6 +28,7 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 constexpr size_t kStageBudget = 48 * 1024;  // raw tile staging bytes (all columns)
+constexpr int kOffRegs = (PX_MAX_PARTS + kThreads - 1) / kThreads;  // partitions per thread, at most
 
 constexpr int kScanThreads = 256;
 constexpr int kScanItems = 8;
@@ -204,6 +205,14 @@ part_scatter_kernel(Cols cols, int32_t key_col, const int32_t* __restrict__ sel,
     const int64_t rem = n - tbase;
     const int tile_rows = rem <= 0 ? 0 : (rem < T ? static_cast<int>(rem) : T);
     for (int k = tid; k < kWarps * np1; k += kThreads) s_whist[k] = 0;
+    // This tile's output start in each partition (one strided load per partition),
+    // requested now so its latency hides behind the staging of the tile.
+    int32_t my_off[kOffRegs];
+#pragma unroll
+    for (int r = 0; r < kOffRegs; ++r) {
+        const int q = tid + r * kThreads;
+        my_off[r] = q < static_cast<int>(nparts) ? offs[static_cast<int64_t>(q) * ntiles + tile] : 0;
+    }
 
     // Stage the tile of every column: TMA bulk copies for a full contiguous tile,
     // plain loads for a gather through a selection or a ragged last tile.
@@ -278,8 +287,11 @@ part_scatter_kernel(Cols cols, int32_t key_col, const int32_t* __restrict__ sel,
     }
     __syncthreads();
     block_excl_scan_smem(s_tstart, static_cast<int>(nparts), s_warp);
-    for (int q = tid; q < static_cast<int>(nparts); q += kThreads)
-        s_delta[q] = offs[static_cast<int64_t>(q) * ntiles + tile] - s_tstart[q];
+#pragma unroll
+    for (int r = 0; r < kOffRegs; ++r) {
+        const int q = tid + r * kThreads;
+        if (q < static_cast<int>(nparts)) s_delta[q] = my_off[r] - s_tstart[q];
+    }
 #pragma unroll
     for (int i = 0; i < ITEMS; ++i) {
         if (pidv[i] < nparts) {
