@@ -260,17 +260,12 @@ __device__ __forceinline__ void cursor_seek(SegCursor& c, const TableView& t, co
 
 // Looks `key` up in the 4 keys k01, k23 of one bucket: the lane of the match, or
 // -1 with *end set when an empty slot ends the probe sequence in this bucket.
+// Occupied slots form a prefix of every probe sequence (inserts take the first
+// empty slot), so a present key precedes the first empty slot. Branch-free.
 __device__ __forceinline__ int bucket_find(longlong2 k01, longlong2 k23, int64_t key, bool* end) {
-    *end = false;
-    if (k01.x == key) return 0;
-    if (k01.x == kEmpty) { *end = true; return -1; }
-    if (k01.y == key) return 1;
-    if (k01.y == kEmpty) { *end = true; return -1; }
-    if (k23.x == key) return 2;
-    if (k23.x == kEmpty) { *end = true; return -1; }
-    if (k23.y == key) return 3;
-    if (k23.y == kEmpty) { *end = true; return -1; }
-    return -1;
+    const int l = k01.x == key ? 0 : (k01.y == key ? 1 : (k23.x == key ? 2 : (k23.y == key ? 3 : -1)));
+    *end = l < 0 && (k01.x == kEmpty || k01.y == kEmpty || k23.x == kEmpty || k23.y == kEmpty);
+    return l;
 }
 
 constexpr int kMatchWarps = kMatchThreads / 32;
