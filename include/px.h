@@ -258,6 +258,71 @@ px_status px_groupby_agg(const px_batch* in, const int32_t* key_cols, int32_t nk
                          int64_t max_groups, const px_batch* out, int32_t* d_out_seg,
                          int64_t* d_ngroups, void* d_ws, size_t ws_bytes, void* stream);
 
+/* ---- batched fused fragments: filter -> probe -> aggregate ------------- */
+/* The paper runs many small plan fragments whose vectors are too small to fill a
+ * GPU (Sec. 3.3.2; batch-size sensitivity, Sec. 3.4). This entry point runs a
+ * batch of independent Q5/Q9-shaped fragments (FilterProject -> join probe ->
+ * HashAggregation in Single mode) in ONE persistent kernel that pulls
+ * (fragment, row chunk) work items from a device counter, plus one emit kernel.
+ *
+ * Fragment f: over its probe rows i < nrows keep those with
+ * filter.lo <= filter[i] < filter.hi (all rows when filter.data is NULL), look
+ * key[i] up in d_table (a unique, unsegmented table from px_join_build), and for
+ * every match with build row r GROUP BY group[r] (a build-side column indexed by
+ * build row), computing aggs over the probe columns cols[] (px_agg.a / .b index
+ * cols). group_lo..group_hi is REQUIRED and is a guarantee (unlike px_key_range):
+ * a matched row whose group key lies outside records PX_ERR_UNSUPPORTED and is
+ * skipped. Results: the groups in ascending key order, keys in d_out_keys (type
+ * group.type) and aggregates in d_out_aggs[a] (PX_I64), capacity max_groups;
+ * *d_ngroups receives the group count (over capacity: PX_ERR_CAPACITY, first
+ * max_groups written). A fragment's result does not depend on the other fragments
+ * of the batch or on the configuration. */
+#define PX_FRAG_MAX_COLS 4
+#define PX_FRAG_MAX_AGGS 4
+#define PX_FRAG_MAX_GROUPS (1LL << 22) /* group_hi - group_lo + 1 at most */
+typedef struct {
+    int64_t nrows;                            /* probe rows (< 2^31) */
+    px_col key;                               /* PX_I64 join key */
+    px_col filter;                            /* PX_I8/I32/I64; data NULL: no filter */
+    int64_t lo, hi;                           /* keep lo <= filter < hi */
+    int32_t ncols;                            /* 0..PX_FRAG_MAX_COLS */
+    int32_t naggs;                            /* 0..PX_FRAG_MAX_AGGS */
+    px_col cols[PX_FRAG_MAX_COLS];            /* probe columns the aggregates read */
+    px_agg aggs[PX_FRAG_MAX_AGGS];
+    const void* d_table;                      /* unique, unsegmented join table */
+    int64_t nbuild;                           /* build rows: the length of group */
+    px_col group;                             /* build column: the group key */
+    int64_t group_lo, group_hi;               /* every group key lies in [group_lo, group_hi] */
+    int64_t max_groups;                       /* output capacity */
+    void* d_out_keys;                         /* group.type, capacity max_groups */
+    int64_t* d_out_aggs[PX_FRAG_MAX_AGGS];    /* PX_I64, capacity max_groups each */
+    int64_t* d_ngroups;                       /* device int64 */
+} px_fragment;
+
+/* Launch configuration of px_fragments_run (NULL: library defaults). threads per
+ * block (256 or 512), items per thread (4 or 8), rows per work item (a multiple
+ * of threads * items; fragments whose dense accumulators live in shared memory
+ * take at least 4 group slots' worth of rows per item), and resident blocks per
+ * SM of the persistent grid (1..8; capped by what fits). A project autotuner
+ * picks these per GPU; every configuration gives the same results. */
+typedef struct {
+    int32_t threads;
+    int32_t items;
+    int64_t chunk_rows;
+    int32_t blocks_per_sm;
+} px_fragments_config;
+
+/* Host staging bytes for the plan of nfrags fragments (see px_fragments_run). */
+size_t px_fragments_plan_bytes(int32_t nfrags);
+size_t px_fragments_ws_bytes(const px_fragment* frags, int32_t nfrags);
+
+/* Run nfrags fragments as one batch. h_plan (px_fragments_plan_bytes bytes, HOST
+ * memory, pinned for an asynchronous upload) receives the device plan, which is
+ * copied into d_ws on `stream`; it must stay unchanged until the stream work has
+ * completed. */
+px_status px_fragments_run(const px_fragment* frags, int32_t nfrags, const px_fragments_config* cfg,
+                           void* h_plan, size_t plan_bytes, void* d_ws, size_t ws_bytes, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -222,6 +222,19 @@ def pipeline_join(d: dict, lo: int, hi: int) -> dict:
     return {"sel": sel, "probe_rows": pr, "build_rows": br, "groups": g}
 
 
+def pipeline_fragment(d: dict, lo: int, hi: int) -> dict:
+    """One batched fragment (FilterProject -> join probe -> Single-mode
+    HashAggregation, Sec. 3.2 operators in a Q5/Q9-like plan, Sec. 3.4): keep fact
+    rows with lo <= date < hi, join key = pk, group by dim.attr with SUM(price),
+    SUM(price * qty), COUNT(*). Groups in ascending attr order."""
+    sel = filter(d["date"], lo, hi)
+    pr, br, _ = join(d["pk"], d["key"], sel=sel)
+    attr = d["attr"][br]
+    g = groupby([attr], [(SUM, d["price"][pr], None), (SUM_MUL, d["price"][pr], d["qty"][pr]),
+                         (COUNT, None, None)])
+    return {"sel": sel, "probe_rows": pr, "build_rows": br, "groups": g}
+
+
 def pipeline_at_scale(d: dict, nparts: int, seed: int = 0) -> dict:
     """Exchange-join-aggregate at scale (Sec. 3.3 exchange feeding per-partition joins
     and Partial aggregation, then a Final merge, Sec. 3.2): partition dim on pk and

@@ -34,7 +34,9 @@ EXPORTED = [
     "px_join_table_bytes", "px_join_build_ws_bytes", "px_join_build",
     "px_join_probe_ws_bytes", "px_join_probe",
     "px_groupby_ws_bytes", "px_groupby_agg",
+    "px_fragments_plan_bytes", "px_fragments_ws_bytes", "px_fragments_run",
 ]
+PX_FRAG_MAX_COLS, PX_FRAG_MAX_AGGS, PX_FRAG_MAX_GROUPS = 4, 4, 1 << 22
 
 _TYPES = {torch.int8: PX_I8, torch.int32: PX_I32, torch.int64: PX_I64}
 
@@ -60,6 +62,20 @@ class px_agg(ctypes.Structure):
 
 class px_key_range(ctypes.Structure):
     _fields_ = [("lo", ctypes.c_int64 * 2), ("hi", ctypes.c_int64 * 2)]
+
+
+class px_fragment(ctypes.Structure):
+    _fields_ = [("nrows", ctypes.c_int64), ("key", px_col), ("filter", px_col), ("lo", ctypes.c_int64),
+                ("hi", ctypes.c_int64), ("ncols", ctypes.c_int32), ("naggs", ctypes.c_int32),
+                ("cols", px_col * 4), ("aggs", px_agg * 4), ("d_table", ctypes.c_void_p),
+                ("nbuild", ctypes.c_int64), ("group", px_col), ("group_lo", ctypes.c_int64),
+                ("group_hi", ctypes.c_int64), ("max_groups", ctypes.c_int64), ("d_out_keys", ctypes.c_void_p),
+                ("d_out_aggs", ctypes.c_void_p * 4), ("d_ngroups", ctypes.c_void_p)]
+
+
+class px_fragments_config(ctypes.Structure):
+    _fields_ = [("threads", ctypes.c_int32), ("items", ctypes.c_int32), ("chunk_rows", ctypes.c_int64),
+                ("blocks_per_sm", ctypes.c_int32)]
 
 
 _lib = None
@@ -88,6 +104,10 @@ def _declare(lib):
         "px_groupby_ws_bytes": ([I64, I64], SZ),
         "px_groupby_agg": ([BP, P, I32, AP, I32, P, P, P, I32, ctypes.POINTER(px_key_range), I64, BP, P, P, P,
                             SZ, P], I32),
+        "px_fragments_plan_bytes": ([I32], SZ),
+        "px_fragments_ws_bytes": ([ctypes.POINTER(px_fragment), I32], SZ),
+        "px_fragments_run": ([ctypes.POINTER(px_fragment), I32, ctypes.POINTER(px_fragments_config), P, SZ, P, SZ, P],
+                             I32),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -339,3 +359,69 @@ def px_groupby_agg(cols, key_cols, aggs, *, max_groups: int, sel=None, nsel=None
                             _ptr(res.get("seg")), _ptr(res["ngroups"]), ws.ptr, ws.nbytes, _stream(stream)),
            "px_groupby_agg")
     return res
+
+
+class FragmentBatch:
+    """A batch of fused filter -> join probe -> aggregate fragments (px_fragments_run).
+
+    Each fragment is a dict with: key (int64 probe join-key column), filter (column
+    or None), lo, hi (keep lo <= filter < hi), cols (probe columns the aggregates
+    read), aggs [(op, a, b)], table (a unique unsegmented table from px_join_build),
+    group (build column holding the group key, indexed by build row), group_lo,
+    group_hi (every group key lies in that range) and max_groups. Outputs are
+    allocated once; run() may be called again (one run in flight per batch). The
+    pinned plan staging buffer lives with the batch."""
+
+    def __init__(self, frags: list, config: tuple | None = None, ws: Workspace | None = None):
+        L = load()
+        self.n = len(frags)
+        self.frags = frags
+        dev = frags[0]["key"].device if frags else torch.device("cuda", torch.cuda.current_device())
+        arr = (px_fragment * max(1, self.n))()
+        self.results = []
+        self._keep = []
+        for i, f in enumerate(frags):
+            d = arr[i]
+            key = f["key"]
+            d.nrows = key.numel()
+            d.key = _col(key)
+            if f.get("filter") is not None:
+                d.filter = _col(f["filter"])
+                d.lo, d.hi = int(f["lo"]), int(f["hi"])
+            cols = list(f.get("cols", []))
+            d.ncols = len(cols)
+            for c, t in enumerate(cols):
+                d.cols[c] = _col(t)
+            aggs = list(f.get("aggs", []))
+            d.naggs = len(aggs)
+            for a, (op, x, y) in enumerate(aggs):
+                d.aggs[a] = px_agg(op, -1 if x is None else x, -1 if y is None else y)
+            d.d_table = _ptr(f["table"])
+            d.nbuild = f["group"].numel()
+            d.group = _col(f["group"])
+            d.group_lo, d.group_hi = int(f["group_lo"]), int(f["group_hi"])
+            mg = int(f["max_groups"])
+            d.max_groups = mg
+            keys = torch.empty(max(mg, 1), dtype=f["group"].dtype, device=dev)
+            outs = [torch.empty(max(mg, 1), dtype=torch.int64, device=dev) for _ in aggs]
+            ng = torch.zeros(1, dtype=torch.int64, device=dev)
+            d.d_out_keys = keys.data_ptr()
+            for a, t in enumerate(outs):
+                d.d_out_aggs[a] = t.data_ptr()
+            d.d_ngroups = ng.data_ptr()
+            self.results.append({"keys": keys, "aggs": outs, "ngroups": ng})
+            self._keep += [key, f.get("filter"), f["table"], f["group"], *cols]
+        self.arr = arr
+        self.cfg = None
+        if config is not None:
+            self.cfg = px_fragments_config(*config)
+        self.plan = torch.empty(max(1, L.px_fragments_plan_bytes(self.n)), dtype=torch.uint8).pin_memory()
+        need = L.px_fragments_ws_bytes(arr, self.n)
+        self.ws = (ws or Workspace(need, device=dev)).ensure(need)
+
+    def run(self, stream=None):
+        L = load()
+        _check(L.px_fragments_run(self.arr, self.n, ctypes.byref(self.cfg) if self.cfg is not None else None,
+                                  self.plan.data_ptr(), self.plan.numel(), self.ws.ptr, self.ws.nbytes,
+                                  _stream(stream)), "px_fragments_run")
+        return self.results

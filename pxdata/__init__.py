@@ -100,6 +100,40 @@ def plain_at_scale(ndim: int = 2_000_000, nfact: int = 60_000_000, nattr: int = 
     return {"pk": pk, "attr": attr, "fk": fk, "amount": amount, "date": date}
 
 
+def _log_uniform_int(g: np.random.Generator, lo: int, hi: int, size: int) -> np.ndarray:
+    return np.floor(np.exp(g.uniform(np.log(lo), np.log(hi), size=size))).astype(np.int64)
+
+
+def fragment_sizes(nfrags: int = 512, seed: int = 4, scale: float = 1.0) -> dict:
+    """Sizes of the batched-fragments workload: per fragment, fact rows log-uniform
+    in [10^4, 4*10^6], build rows log-uniform in [10^3, 10^6] and group-key domain
+    log-uniform in [4, 10^5], each bound multiplied by `scale` (at least 1; tests
+    use small scales). Drawn in that order."""
+    g = _rng(seed)
+    lo = lambda x: max(1, int(x * scale))
+    return {"nfact": _log_uniform_int(g, lo(1e4), lo(4e6), nfrags),
+            "nbuild": _log_uniform_int(g, lo(1e3), lo(1e6), nfrags),
+            "ngroups": _log_uniform_int(g, 4, max(5, lo(1e5)), nfrags)}
+
+
+def fragment(nfact: int, nbuild: int, ngroups: int, seed: int) -> dict:
+    """One fragment of the batched workload: a dimension and a fact batch with the
+    plain workload's column types.
+
+    dim: pk int64 = seeded permutation of 1..nbuild, attr int32 U[0, ngroups).
+    fact: key int64 U[1, nbuild + nbuild // 20] (about 5 % of keys name no pk),
+    price int64 U[100, 10^7] (scale 2), qty int64 U[1, 50], date int32 U[0, 2557).
+    """
+    g = _rng(seed)
+    pk = g.permutation(nbuild).astype(np.int64) + 1
+    attr = g.integers(0, ngroups, size=nbuild, dtype=np.int32)
+    key = g.integers(1, nbuild + nbuild // 20, size=nfact, dtype=np.int64, endpoint=True)
+    price = g.integers(100, 10**7, size=nfact, dtype=np.int64, endpoint=True)
+    qty = g.integers(1, 50, size=nfact, dtype=np.int64, endpoint=True)
+    date = g.integers(0, DATE_DAYS, size=nfact, dtype=np.int32)
+    return {"pk": pk, "attr": attr, "key": key, "price": price, "qty": qty, "date": date}
+
+
 def random_column(g: np.random.Generator, n: int, dtype, lo=None, hi=None) -> np.ndarray:
     """A column of n values of `dtype` uniform in [lo, hi] (default: the full type range)."""
     info = np.iinfo(dtype)
