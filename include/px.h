@@ -300,7 +300,7 @@ typedef struct {
 } px_fragment;
 
 /* Launch configuration of px_fragments_run (NULL: library defaults). threads per
- * block (256 or 512), items per thread (4 or 8), rows per work item (a multiple
+ * block (256 or 512), items per thread (2 or 4), rows per work item (a multiple
  * of threads * items; fragments whose dense accumulators live in shared memory
  * take at least 4 group slots' worth of rows per item), and resident blocks per
  * SM of the persistent grid (1..8; capped by what fits). A project autotuner

@@ -419,9 +419,11 @@ class FragmentBatch:
         need = L.px_fragments_ws_bytes(arr, self.n)
         self.ws = (ws or Workspace(need, device=dev)).ensure(need)
 
-    def run(self, stream=None):
+    def run(self, stream=None, config: tuple | None = None):
+        """Launch the batch (config overrides the batch's launch configuration)."""
         L = load()
-        _check(L.px_fragments_run(self.arr, self.n, ctypes.byref(self.cfg) if self.cfg is not None else None,
+        cfg = px_fragments_config(*config) if config is not None else self.cfg
+        _check(L.px_fragments_run(self.arr, self.n, ctypes.byref(cfg) if cfg is not None else None,
                                   self.plan.data_ptr(), self.plan.numel(), self.ws.ptr, self.ws.nbytes,
                                   _stream(stream)), "px_fragments_run")
         return self.results

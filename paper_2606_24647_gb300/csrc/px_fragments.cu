@@ -39,9 +39,10 @@ struct FragDev {
     const void* filter;
     int64_t lo, hi;
     int64_t nrows;
-    const void* col[PX_FRAG_MAX_COLS];
-    int32_t col_w[PX_FRAG_MAX_COLS];
-    int32_t op[PX_FRAG_MAX_AGGS], a[PX_FRAG_MAX_AGGS], b[PX_FRAG_MAX_AGGS];
+    // aggregate k reads column pa[k] (width wa[k]) and, for SUM_MUL, pb[k] (wb[k])
+    const void* pa[PX_FRAG_MAX_AGGS];
+    const void* pb[PX_FRAG_MAX_AGGS];
+    int32_t op[PX_FRAG_MAX_AGGS], wa[PX_FRAG_MAX_AGGS], wb[PX_FRAG_MAX_AGGS];
     int32_t filter_w, naggs, group_w, count_agg;  // count_agg: a COUNT aggregate, or -1
     TableView t;
     int64_t nbuild;
@@ -119,14 +120,14 @@ __device__ __forceinline__ int32_t probe_row(const TableView& t, uint32_t nb, in
 
 // Rows [r0, r1) of fragment f. SHARED: accumulate into the block arrays lo/hi
 // ([naggs][D] each) and occupancy bits; else reduce into the global arrays.
-template <int THREADS, int ITEMS, bool SHARED>
+template <int THREADS, int ITEMS, int NA, bool SHARED>
 __device__ void frag_rows(const FragDev& f, int64_t r0, int64_t r1, uint32_t* s_lo, uint32_t* s_hi,
                           uint32_t* s_occ, int32_t* status) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t nb = static_cast<uint32_t>(table_buckets(f.t.hdr->nbuild, 1));
     const int naggs = f.naggs;
     for (int64_t tb = r0; tb < r1; tb += THREADS * ITEMS) {
-        int64_t key[ITEMS], v[PX_FRAG_MAX_AGGS][ITEMS];
+        int64_t key[ITEMS], v[NA][ITEMS];
         bool pass[ITEMS];
 #pragma unroll
         for (int i = 0; i < ITEMS; ++i) {
@@ -140,14 +141,14 @@ __device__ void frag_rows(const FragDev& f, int64_t r0, int64_t r1, uint32_t* s_
             pass[i] = p;
             key[i] = valid ? f.key[r] : kEmpty;
 #pragma unroll
-            for (int a = 0; a < PX_FRAG_MAX_AGGS; ++a) {
+            for (int a = 0; a < NA; ++a) {
                 if (a >= naggs) break;
                 int64_t x = 1;
                 if (f.op[a] != PX_COUNT && valid) {
-                    x = load_w(f.col[f.a[a]], f.col_w[f.a[a]], r);
+                    x = load_w(f.pa[a], f.wa[a], r);
                     if (f.op[a] == PX_SUM_MUL)
                         x = static_cast<int64_t>(static_cast<uint64_t>(x) *
-                                                 static_cast<uint64_t>(load_w(f.col[f.b[a]], f.col_w[f.b[a]], r)));
+                                                 static_cast<uint64_t>(load_w(f.pb[a], f.wb[a], r)));
                 }
                 v[a][i] = x;
             }
@@ -172,7 +173,7 @@ __device__ void frag_rows(const FragDev& f, int64_t r0, int64_t r1, uint32_t* s_
             if (c0 != 0xffffffffu && __popc(mm) >= kMajority) {
                 const bool in = (mm >> lane) & 1u;
 #pragma unroll
-                for (int a = 0; a < PX_FRAG_MAX_AGGS; ++a) {
+                for (int a = 0; a < NA; ++a) {
                     if (a >= naggs) break;
                     const int64_t x = warp_sum(in ? v[a][i] : int64_t(0));
                     if (lane == 0) v[a][i] = x;
@@ -182,7 +183,7 @@ __device__ void frag_rows(const FragDev& f, int64_t r0, int64_t r1, uint32_t* s_
             if (apply == 0xffffffffu) continue;
             if (SHARED) {
 #pragma unroll
-                for (int a = 0; a < PX_FRAG_MAX_AGGS; ++a) {
+                for (int a = 0; a < NA; ++a) {
                     if (a >= naggs) break;
                     const size_t o = static_cast<size_t>(a) * f.D + apply;
                     add_split(&s_lo[o], &s_hi[o], static_cast<uint64_t>(v[a][i]));
@@ -190,7 +191,7 @@ __device__ void frag_rows(const FragDev& f, int64_t r0, int64_t r1, uint32_t* s_
                 if (f.count_agg < 0) red_or_shared(&s_occ[apply / 32], 1u << (apply % 32));
             } else {
 #pragma unroll
-                for (int a = 0; a < PX_FRAG_MAX_AGGS; ++a) {
+                for (int a = 0; a < NA; ++a) {
                     if (a >= naggs) break;
                     red_add_global(&f.acc[static_cast<size_t>(a) * f.D + apply], static_cast<unsigned long long>(v[a][i]));
                 }
@@ -201,22 +202,36 @@ __device__ void frag_rows(const FragDev& f, int64_t r0, int64_t r1, uint32_t* s_
 }
 
 // Persistent fused kernel: (fragment, chunk) work items from a device counter.
-template <int THREADS, int ITEMS>
+template <int THREADS, int ITEMS, int NA>
 __global__ void __launch_bounds__(THREADS)
 frag_kernel(const PlanHeader* __restrict__ ph, const int64_t* __restrict__ item_start, const FragDev* __restrict__ fd,
             unsigned long long* counter, int32_t* status) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int64_t s_item;
+    __shared__ int32_t s_p;
+    // The work item's fragment plan, copied to shared memory once per item: the
+    // reductions' memory clobbers would otherwise reload its fields from global
+    // memory after every update.
+    __shared__ __align__(16) FragDev s_f;
     const int n = ph->nfrags;
     const int64_t nitems = ph->nitems;
     for (;;) {
-        if (threadIdx.x == 0) s_item = static_cast<int64_t>(atomicAdd(counter, 1ull));
+        if (threadIdx.x == 0) {
+            const int64_t it = static_cast<int64_t>(atomicAdd(counter, 1ull));
+            s_item = it;
+            s_p = it < nitems ? find_frag(item_start, n, it) : 0;
+        }
         __syncthreads();
         const int64_t item = s_item;
+        const int p = s_p;
+        if (item < nitems) {
+            const uint32_t* src = reinterpret_cast<const uint32_t*>(&fd[p]);
+            uint32_t* dst = reinterpret_cast<uint32_t*>(&s_f);
+            for (int w = threadIdx.x; w < static_cast<int>(sizeof(FragDev) / 4); w += THREADS) dst[w] = src[w];
+        }
         __syncthreads();
         if (item >= nitems) break;
-        const int p = find_frag(item_start, n, item);
-        const FragDev& f = fd[p];
+        const FragDev& f = s_f;
         // A table this fragment cannot use: its rows are skipped.
         if (f.t.hdr->magic != kMagic || f.t.hdr->nsegs != 1 || f.t.hdr->unique == 0 || f.t.hdr->nbuild > f.nbuild) {
             if (threadIdx.x == 0) set_status(status, PX_ERR_INVALID);
@@ -225,7 +240,7 @@ frag_kernel(const PlanHeader* __restrict__ ph, const int64_t* __restrict__ item_
         const int64_t r0 = (item - item_start[p]) * f.chunk;
         const int64_t r1 = r0 + f.chunk < f.nrows ? r0 + f.chunk : f.nrows;
         if (!f.shared) {
-            frag_rows<THREADS, ITEMS, false>(f, r0, r1, nullptr, nullptr, nullptr, status);
+            frag_rows<THREADS, ITEMS, NA, false>(f, r0, r1, nullptr, nullptr, nullptr, status);
             continue;
         }
         const uint32_t D = f.D;
@@ -236,7 +251,7 @@ frag_kernel(const PlanHeader* __restrict__ ph, const int64_t* __restrict__ item_
         const uint32_t words = 2 * naggs * D + (f.count_agg < 0 ? (D + 31) / 32 : 0);
         for (uint32_t w = threadIdx.x; w < words; w += THREADS) s_lo[w] = 0;
         __syncthreads();
-        frag_rows<THREADS, ITEMS, true>(f, r0, r1, s_lo, s_hi, s_occ, status);
+        frag_rows<THREADS, ITEMS, NA, true>(f, r0, r1, s_lo, s_hi, s_occ, status);
         __syncthreads();
         for (uint32_t d = threadIdx.x; d < D; d += THREADS) {
             bool occ = f.count_agg < 0 && ((s_occ[d / 32] >> (d % 32)) & 1u);
@@ -379,10 +394,10 @@ px_status check_fragment(const px_fragment& f, int32_t i) {
     return PX_OK;
 }
 
-template <int THREADS, int ITEMS>
-px_status launch_frag(const PlanHeader* ph, const int64_t* item_start, const FragDev* fd, unsigned long long* counter,
-                      int32_t* status, size_t smem, int bps, cudaStream_t st) {
-    auto kernel = frag_kernel<THREADS, ITEMS>;
+template <int THREADS, int ITEMS, int NA>
+px_status launch_frag_na(const PlanHeader* ph, const int64_t* item_start, const FragDev* fd,
+                         unsigned long long* counter, int32_t* status, size_t smem, int bps, cudaStream_t st) {
+    auto kernel = frag_kernel<THREADS, ITEMS, NA>;
     if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)) !=
         cudaSuccess)
         return check_launch("px_fragments_run attribute");
@@ -393,6 +408,19 @@ px_status launch_frag(const PlanHeader* ph, const int64_t* item_start, const Fra
     kernel<<<blocks, THREADS, smem, st>>>(ph, item_start, fd, counter, status);
     note_launch();
     return check_launch("px_fragments_run fused");
+}
+
+// NA: the batch's largest aggregate count (at least 1), a compile-time bound.
+template <int THREADS, int ITEMS>
+px_status launch_frag(int na, const PlanHeader* ph, const int64_t* item_start, const FragDev* fd,
+                      unsigned long long* counter, int32_t* status, size_t smem, int bps, cudaStream_t st) {
+    switch (na) {
+        case 0:
+        case 1: return launch_frag_na<THREADS, ITEMS, 1>(ph, item_start, fd, counter, status, smem, bps, st);
+        case 2: return launch_frag_na<THREADS, ITEMS, 2>(ph, item_start, fd, counter, status, smem, bps, st);
+        case 3: return launch_frag_na<THREADS, ITEMS, 3>(ph, item_start, fd, counter, status, smem, bps, st);
+        default: return launch_frag_na<THREADS, ITEMS, 4>(ph, item_start, fd, counter, status, smem, bps, st);
+    }
 }
 
 }  // namespace
@@ -418,9 +446,9 @@ px_status px_fragments_run(const px_fragment* frags, int32_t nfrags, const px_fr
         const px_status s = check_fragment(frags[i], i);
         if (s != PX_OK) return s;
     }
-    px_fragments_config c = {256, 4, 65536, 8};
+    px_fragments_config c = {256, 2, 65536, 8};
     if (cfg) c = *cfg;
-    if ((c.threads != 256 && c.threads != 512) || (c.items != 4 && c.items != 8) || c.blocks_per_sm < 1 ||
+    if ((c.threads != 256 && c.threads != 512) || (c.items != 2 && c.items != 4) || c.blocks_per_sm < 1 ||
         c.blocks_per_sm > 8 || c.chunk_rows < 1 || c.chunk_rows % (static_cast<int64_t>(c.threads) * c.items) != 0)
         return fail(PX_ERR_INVALID, "px_fragments_run: bad configuration");
     const PlanLayout PL = plan_layout(nfrags);
@@ -467,17 +495,20 @@ px_status px_fragments_run(const px_fragment* frags, int32_t nfrags, const px_fr
         d.lo = f.lo;
         d.hi = f.hi;
         d.nrows = f.nrows;
-        for (int cc = 0; cc < f.ncols; ++cc) {
-            d.col[cc] = f.cols[cc].data;
-            d.col_w[cc] = f.cols[cc].type;
-        }
         d.naggs = f.naggs;
         d.count_agg = -1;
         for (int a = 0; a < f.naggs; ++a) {
-            d.op[a] = f.aggs[a].op;
-            d.a[a] = f.aggs[a].a;
-            d.b[a] = f.aggs[a].b;
-            if (f.aggs[a].op == PX_COUNT && d.count_agg < 0) d.count_agg = a;
+            const px_agg& g = f.aggs[a];
+            d.op[a] = g.op;
+            if (g.op != PX_COUNT) {
+                d.pa[a] = f.cols[g.a].data;
+                d.wa[a] = f.cols[g.a].type;
+            }
+            if (g.op == PX_SUM_MUL) {
+                d.pb[a] = f.cols[g.b].data;
+                d.wb[a] = f.cols[g.b].type;
+            }
+            if (g.op == PX_COUNT && d.count_agg < 0) d.count_agg = a;
         }
         d.t = table_view(const_cast<void*>(f.d_table), 1);
         d.nbuild = f.nbuild;
@@ -525,10 +556,16 @@ px_status px_fragments_run(const px_fragment* frags, int32_t nfrags, const px_fr
     const int64_t* d_emits = reinterpret_cast<const int64_t*>(dplan + PL.emits);
     const FragDev* d_fd = reinterpret_cast<const FragDev*>(dplan + PL.frags);
     if (items > 0) {
-        if (c.threads == 256 && c.items == 4) s = launch_frag<256, 4>(d_ph, d_items, d_fd, counters, status, smem, c.blocks_per_sm, st);
-        else if (c.threads == 256) s = launch_frag<256, 8>(d_ph, d_items, d_fd, counters, status, smem, c.blocks_per_sm, st);
-        else if (c.items == 4) s = launch_frag<512, 4>(d_ph, d_items, d_fd, counters, status, smem, c.blocks_per_sm, st);
-        else s = launch_frag<512, 8>(d_ph, d_items, d_fd, counters, status, smem, c.blocks_per_sm, st);
+        int na = 0;
+        for (int32_t i = 0; i < nfrags; ++i) na = std::max(na, frags[i].naggs);
+        if (c.threads == 256 && c.items == 2)
+            s = launch_frag<256, 2>(na, d_ph, d_items, d_fd, counters, status, smem, c.blocks_per_sm, st);
+        else if (c.threads == 256)
+            s = launch_frag<256, 4>(na, d_ph, d_items, d_fd, counters, status, smem, c.blocks_per_sm, st);
+        else if (c.items == 2)
+            s = launch_frag<512, 2>(na, d_ph, d_items, d_fd, counters, status, smem, c.blocks_per_sm, st);
+        else
+            s = launch_frag<512, 4>(na, d_ph, d_items, d_fd, counters, status, smem, c.blocks_per_sm, st);
         if (s != PX_OK) return s;
     }
     frag_emit_kernel<<<static_cast<unsigned>(emits), kEmitThreads, 0, st>>>(d_ph, d_emits, d_fd, counters + 1, status);

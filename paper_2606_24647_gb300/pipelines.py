@@ -10,13 +10,16 @@ never synchronises with the host).
                        join build and probe -> Partial group-by per partition -> Final
                        merge (the exchange feeding the join and aggregation, Sec. 3.3
                        with the aggregation modes of Sec. 3.2).
+* FragmentSet        - many small filter -> join -> aggregate fragments over resident
+                       dimension tables, run as one fused batch (px_fragments_run);
+  OneAtATime         - the same fragments one at a time through the unfused calls.
 """
 from __future__ import annotations
 
 import torch
 
-from . import (PX_COUNT, PX_SUM, PX_SUM_MUL, Workspace, load, px_filter, px_groupby_agg, px_join_build,
-               px_join_probe, px_partition)
+from . import (PX_COUNT, PX_SUM, PX_SUM_MUL, FragmentBatch, Workspace, load, px_filter, px_groupby_agg,
+               px_join_build, px_join_probe, px_partition)
 
 
 def _empty_like_cols(cols, n=None):
@@ -153,3 +156,71 @@ class AtScalePipeline:
                                d_nrows=part["ngroups"], key_range=rng, out=self.fout, ws=ws, stream=stream)
         mark(6)
         return {"dim_offsets": self.doff, "fact_offsets": self.foff, "join": j, "partial": part, "final": final}
+
+
+class FragmentSet:
+    """Device-resident fragments of the batched workload: per fragment its fact
+    columns, its dimension columns and its unique join table (built once, as a
+    resident dimension table). Query of every fragment: keep date in [lo, hi),
+    join key = pk, group by dim.attr (values 0..ngroups-1): SUM(price),
+    SUM(price * qty), COUNT(*)."""
+
+    def __init__(self, datas: list, ngroups: list, lo: int, hi: int, device=None, stream=None):
+        L = load()
+        dev = device or torch.device("cuda", torch.cuda.current_device())
+        self.lo, self.hi = lo, hi
+        self.ngroups = [int(g) for g in ngroups]
+        self.cols, self.frags = [], []
+        ws = Workspace(L.px_join_build_ws_bytes(1), device=dev)
+        for d, ng in zip(datas, self.ngroups):
+            c = {k: torch.from_numpy(d[k]).to(dev, non_blocking=True) for k in ("key", "price", "qty", "date", "pk", "attr")}
+            c["table"] = torch.empty(L.px_join_table_bytes(max(1, d["pk"].size), 0), dtype=torch.uint8, device=dev)
+            px_join_build([c["pk"], c["attr"]], 0, unique=True, table=c["table"], ws=ws, stream=stream)
+            self.cols.append(c)
+            self.frags.append({"key": c["key"], "filter": c["date"], "lo": lo, "hi": hi,
+                               "cols": [c["price"], c["qty"]],
+                               "aggs": [(PX_SUM, 0, None), (PX_SUM_MUL, 0, 1), (PX_COUNT, None, None)],
+                               "table": c["table"], "group": c["attr"], "group_lo": 0, "group_hi": ng - 1,
+                               "max_groups": ng})
+        self.rows = sum(int(c["key"].numel()) for c in self.cols)
+
+    def batch(self, idx=None, config=None, ws=None) -> FragmentBatch:
+        frags = self.frags if idx is None else [self.frags[i] for i in idx]
+        return FragmentBatch(frags, config=config, ws=ws)
+
+
+class OneAtATime:
+    """The same fragments run one at a time through the unfused calls
+    (px_filter -> px_join_probe -> px_groupby_agg), every buffer allocated once
+    and shared across fragments (they run in order on one stream)."""
+
+    def __init__(self, fs: FragmentSet):
+        L = load()
+        self.fs = fs
+        dev = fs.cols[0]["key"].device
+        nmax = max(1, max(int(c["key"].numel()) for c in fs.cols))
+        gmax = max(fs.ngroups)
+        self.sel = torch.empty(nmax, dtype=torch.int32, device=dev)
+        self.nsel = torch.empty(1, dtype=torch.int64, device=dev)
+        self.jout = [torch.empty(nmax, dtype=torch.int64, device=dev), torch.empty(nmax, dtype=torch.int64, device=dev),
+                     torch.empty(nmax, dtype=torch.int32, device=dev)]
+        self.gout = [[torch.empty(g, dtype=torch.int32, device=dev)] +
+                     [torch.empty(g, dtype=torch.int64, device=dev) for _ in range(3)] for g in fs.ngroups]
+        need = max(L.px_filter_ws_bytes(nmax), L.px_join_probe_ws_bytes(nmax), L.px_groupby_ws_bytes(nmax, gmax))
+        self.ws = Workspace(need, device=dev)
+        self.results = [None] * len(fs.cols)
+
+    def run(self, stream=None, idx=None):
+        fs = self.fs
+        for i in (range(len(fs.cols)) if idx is None else idx):
+            c = fs.cols[i]
+            px_filter(c["date"], fs.lo, fs.hi, sel=self.sel, nsel=self.nsel, ws=self.ws, stream=stream)
+            j = px_join_probe(c["table"], [c["key"], c["price"], c["qty"]], 0, sel=self.sel, nsel=self.nsel,
+                              carry=[1, 2], payload=[c["attr"]], out=self.jout, out_cap=self.jout[0].numel(),
+                              ws=self.ws, stream=stream)
+            ng = fs.ngroups[i]
+            self.results[i] = px_groupby_agg(self.jout, [2], [(PX_SUM, 0, None), (PX_SUM_MUL, 0, 1),
+                                                             (PX_COUNT, None, None)],
+                                             max_groups=ng, d_nrows=j["nout"], key_range=[(0, ng - 1)],
+                                             out=self.gout[i], ws=self.ws, stream=stream)
+        return self.results

@@ -72,7 +72,7 @@ def test_fragments_parity_mixed_batch(px):
         _check(r, _want(d))
 
 
-@pytest.mark.parametrize("cfg", [(256, 4, 1024, 8), (256, 8, 2048, 2), (512, 4, 4096, 1), (512, 8, 65536, 2)])
+@pytest.mark.parametrize("cfg", [(256, 2, 512, 8), (256, 4, 2048, 2), (512, 2, 4096, 1), (512, 4, 65536, 2)])
 def test_fragments_results_do_not_depend_on_config(px, cfg):
     datas, frags = _mixed_batch(px, nfrags=12, seed=41)
     fb = px.FragmentBatch(frags, config=cfg)
