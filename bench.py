@@ -472,6 +472,96 @@ def run_fragments(args):
     return 0
 
 
+# -------------------------------------------------------- serving workload ----
+SERVE_WORKLOAD = ("served fragment queries: 32 resident dimension tables (1K..2M rows, log-spaced; group domains "
+                  "log-uniform [4, 1e5]); Poisson arrivals of fragment queries (fact rows log-uniform [1e4, 4e6]) "
+                  "and at-scale queries (60M-row Zipf s=1.1 fact over the 2M dimension) at 20:1; filter date in "
+                  "[895, 1662) -> join -> group by attr: SUM(price), SUM(price*qty), COUNT; 120 GB admission budget")
+
+
+def build_serving(npool: int, big: int, scale: float, seed: int = 5):
+    import torch
+    from paper_2606_24647_gb300 import serving
+    g = np.random.Generator(np.random.PCG64(seed))
+    sizes = np.unique(np.logspace(3, np.log10(2e6 * scale if scale < 1 else 2e6), 32).astype(np.int64))
+    ngroups = np.floor(np.exp(g.uniform(np.log(4), np.log(1e5), size=sizes.size))).astype(np.int64)
+    dims, dim_np = [], []
+    for i, (nb, ng) in enumerate(zip(sizes, ngroups)):
+        d = pxdata.fragment(0, int(nb), int(ng), seed=20_000 + i)
+        dims.append(serving.ResidentDim(torch.from_numpy(d["pk"]).cuda(), torch.from_numpy(d["attr"]).cuda(), int(ng)))
+        dim_np.append(d)
+    pool = []  # (dim index, device columns, kind)
+    nf = np.floor(np.exp(g.uniform(np.log(1e4 * scale), np.log(4e6 * scale), size=npool))).astype(np.int64)
+    for i in range(npool):
+        k = int(g.integers(0, len(dims)))
+        d = pxdata.fragment(int(nf[i]), int(sizes[k]), int(ngroups[k]), seed=30_000 + i)
+        pool.append((k, {c: torch.from_numpy(d[c]).cuda() for c in ("key", "price", "qty", "date")}, "fragment"))
+    kb = len(dims) - 1  # the largest (2M-row) dimension
+    for j in range(big):
+        n = int(60_000_000 * scale)
+        gg = np.random.Generator(np.random.PCG64(40_000 + j))
+        pk_of_rank = gg.permutation(dim_np[kb]["pk"])
+        key = pk_of_rank[pxdata.zipf_ranks(gg, pk_of_rank.size, n, 1.1) - 1]
+        d = pxdata.fragment(n, 1, 1, seed=41_000 + j)
+        cols = {"key": torch.from_numpy(key).cuda()}
+        cols.update({c: torch.from_numpy(d[c]).cuda() for c in ("price", "qty", "date")})
+        pool.append((kb, cols, "at-scale"))
+    return dims, pool
+
+
+def make_trace(dims, pool, n, seed):
+    from paper_2606_24647_gb300 import serving
+    g = np.random.Generator(np.random.PCG64(seed))
+    frag_idx = [i for i, p in enumerate(pool) if p[2] == "fragment"]
+    big_idx = [i for i, p in enumerate(pool) if p[2] == "at-scale"]
+    qs = []
+    for q in range(n):
+        i = int(g.choice(big_idx)) if big_idx and g.random() < 1 / 21 else int(g.choice(frag_idx))
+        k, cols, _ = pool[i]
+        qs.append(serving.Query(q, dims[k], cols, pxdata.CFG2_DATE_LO, pxdata.CFG2_DATE_HI))
+    return qs
+
+
+def run_serve(args):
+    """Config 5: continuous batching against one-at-a-time service of the same
+    Poisson arrivals, at 0.5x, 0.8x and 1.0x of the batched server's saturation QPS."""
+    import torch
+    import paper_2606_24647_gb300 as px
+    from paper_2606_24647_gb300 import serving
+
+    torch.cuda.set_device(0)
+    px.load()
+    dims, pool = build_serving(args.serve_pool, args.serve_big, args.frag_scale)
+    torch.cuda.synchronize()
+    budget = 120 * 10**9
+    n = args.serve_queries
+
+    def fresh(seed):
+        return make_trace(dims, pool, n, seed)
+
+    # warm-up, then saturation: everything arrives at once
+    serving.Server(budget, max_batch=512).serve(fresh(1)[:64], np.zeros(64))
+    sat = serving.Server(budget, max_batch=512).serve(fresh(2), np.zeros(n))
+    one_sat = serving.OneAtATimeServer().serve(fresh(2)[: max(32, n // 8)], np.zeros(max(32, n // 8)))
+    levels = []
+    for f in (0.5, 0.8, 1.0):
+        rate = f * sat["qps"]
+        arr = serving.poisson_arrivals(rate, n, seed=int(100 * f))
+        b = serving.Server(budget, max_batch=512).serve(fresh(3), arr)
+        o = serving.OneAtATimeServer().serve(fresh(3), arr)
+        levels.append({"offered_load": f, "offered_qps": rate, "batched": b, "one_at_a_time": o})
+    line = {"metric": "served QPS + p50/p99 latency vs one-at-a-time", "value": sat["qps"], "unit": "queries/s",
+            "n_gpus": 1, "steps": n, "warmup": 64, "ms_per_step": round(1000 / sat["qps"], 4),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+            "data": "synthetic (seeded numpy PCG64; TPC-H-like shapes, no TPC-H data)",
+            "config": {"workload": SERVE_WORKLOAD if args.frag_scale == 1 else
+                       f"REDUCED x{args.frag_scale:g}: " + SERVE_WORKLOAD,
+                       "queries_per_level": n, "pool": len(pool), "resident_dims": len(dims)},
+            "saturation": {"batched": sat, "one_at_a_time": one_sat}, "levels": levels}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -484,7 +574,10 @@ def main(argv=None):
     ap.add_argument("--fact-rows", type=int, default=None,
                     help="smaller fact side for profiling captures (the reported workload is then reduced)")
     ap.add_argument("--dim-rows", type=int, default=None)
-    ap.add_argument("--workload", default="at-scale", choices=["at-scale", "fragments"],
+    ap.add_argument("--serve-queries", type=int, default=1000)
+    ap.add_argument("--serve-pool", type=int, default=64)
+    ap.add_argument("--serve-big", type=int, default=2)
+    ap.add_argument("--workload", default="at-scale", choices=["at-scale", "fragments", "serve"],
                     help="at-scale: the exchange-join-aggregate pipeline (default); fragments: the batched fused "
                          "fragments against one-at-a-time calls")
     ap.add_argument("--fragments", type=int, default=FRAG_N)
@@ -497,6 +590,12 @@ def main(argv=None):
         NFACT = args.fact_rows or NFACT
         NDIM = args.dim_rows or NDIM
         WORKLOAD = f"REDUCED for profiling: {NFACT}-row fact x {NDIM}-row dim; otherwise " + WORKLOAD
+    if args.workload == "serve":
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable": "the oracle reference arm covers the at-scale "
+                              "workload; the serving workload is compared with one-at-a-time GPU service"}))
+            return 0
+        return run_serve(args)
     if args.workload == "fragments":
         if args.impl == "reference":
             print(json.dumps({"impl": "reference", "unavailable": "the oracle reference arm covers the at-scale "

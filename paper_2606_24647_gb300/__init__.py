@@ -372,7 +372,8 @@ class FragmentBatch:
     allocated once; run() may be called again (one run in flight per batch). The
     pinned plan staging buffer lives with the batch."""
 
-    def __init__(self, frags: list, config: tuple | None = None, ws: Workspace | None = None):
+    def __init__(self, frags: list, config: tuple | None = None, ws: Workspace | None = None,
+                 plan: torch.Tensor | None = None):
         L = load()
         self.n = len(frags)
         self.frags = frags
@@ -402,9 +403,12 @@ class FragmentBatch:
             d.group_lo, d.group_hi = int(f["group_lo"]), int(f["group_hi"])
             mg = int(f["max_groups"])
             d.max_groups = mg
-            keys = torch.empty(max(mg, 1), dtype=f["group"].dtype, device=dev)
-            outs = [torch.empty(max(mg, 1), dtype=torch.int64, device=dev) for _ in aggs]
-            ng = torch.zeros(1, dtype=torch.int64, device=dev)
+            if "out" in f:  # caller-provided outputs: (keys, [aggs...], ngroups)
+                keys, outs, ng = f["out"][0], list(f["out"][1]), f["out"][2]
+            else:
+                keys = torch.empty(max(mg, 1), dtype=f["group"].dtype, device=dev)
+                outs = [torch.empty(max(mg, 1), dtype=torch.int64, device=dev) for _ in aggs]
+                ng = torch.zeros(1, dtype=torch.int64, device=dev)
             d.d_out_keys = keys.data_ptr()
             for a, t in enumerate(outs):
                 d.d_out_aggs[a] = t.data_ptr()
@@ -415,7 +419,8 @@ class FragmentBatch:
         self.cfg = None
         if config is not None:
             self.cfg = px_fragments_config(*config)
-        self.plan = torch.empty(max(1, L.px_fragments_plan_bytes(self.n)), dtype=torch.uint8).pin_memory()
+        pb = max(1, L.px_fragments_plan_bytes(self.n))
+        self.plan = plan if plan is not None and plan.numel() >= pb else torch.empty(pb, dtype=torch.uint8).pin_memory()
         need = L.px_fragments_ws_bytes(arr, self.n)
         self.ws = (ws or Workspace(need, device=dev)).ensure(need)
 
