@@ -127,6 +127,15 @@ const char* px_last_error(void);
  * copies are not counted. */
 uint64_t px_kernel_launches(void);
 
+/* Self-test of the bounded device waits (the paper has no counterpart): one
+ * device thread polls the device int32 *d_flag (acquire loads, short sleeps)
+ * until it is nonzero, giving up after spin_limit polls (1..2^24); the device
+ * int32 *d_status receives PX_OK if the flag was seen set, PX_ERR_TIMEOUT if the
+ * wait ran out. Every device-side wait in this library has this shape - bounded,
+ * then a status word and a normal return - so a wait that nothing satisfies
+ * never hangs or faults the device, and the context stays usable. */
+px_status px_selftest_wait(const int32_t* d_flag, uint32_t spin_limit, int32_t* d_status, void* stream);
+
 /* ---- filter (FilterProject's predicate, Sec. 3.2) ----------------------- */
 
 size_t px_filter_ws_bytes(int64_t nrows);

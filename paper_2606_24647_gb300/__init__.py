@@ -28,7 +28,7 @@ PX_I8, PX_I32, PX_I64 = 1, 4, 8
 PX_COUNT, PX_SUM, PX_SUM_MUL = 0, 1, 2
 
 EXPORTED = [
-    "px_ws_init", "px_stream_status", "px_last_error", "px_kernel_launches",
+    "px_ws_init", "px_stream_status", "px_last_error", "px_kernel_launches", "px_selftest_wait",
     "px_filter_ws_bytes", "px_filter", "px_filter_noalloc",
     "px_partition_ws_bytes", "px_partition",
     "px_join_table_bytes", "px_join_build_ws_bytes", "px_join_build",
@@ -91,6 +91,7 @@ def _declare(lib):
         "px_stream_status": ([P, P], I32),
         "px_last_error": ([], ctypes.c_char_p),
         "px_kernel_launches": ([], U64),
+        "px_selftest_wait": ([P, ctypes.c_uint32, P, P], I32),
         "px_filter_ws_bytes": ([I64], SZ),
         "px_filter": ([CP, I64, P, I64, I64, P, P, P, SZ, P], I32),
         "px_filter_noalloc": ([CP, I64, P, I64, I64, P, P, P, P], I32),
@@ -432,3 +433,8 @@ class FragmentBatch:
                                   self.plan.data_ptr(), self.plan.numel(), self.ws.ptr, self.ws.nbytes,
                                   _stream(stream)), "px_fragments_run")
         return self.results
+
+
+def px_selftest_wait(flag: torch.Tensor, spin_limit: int, status: torch.Tensor, stream=None) -> None:
+    """Bounded device wait on flag (int32[1]) -> status (int32[1]): PX_OK or PX_ERR_TIMEOUT."""
+    _check(load().px_selftest_wait(_ptr(flag), int(spin_limit), _ptr(status), _stream(stream)), "px_selftest_wait")

@@ -103,3 +103,33 @@ px_status px_stream_status(void* stream, const void* d_ws) {
 }
 
 }  // extern "C"
+
+namespace px {
+namespace {
+
+__global__ void selftest_wait_kernel(const int32_t* flag, uint32_t limit, int32_t* status) {
+    for (uint32_t i = 0; i < limit; ++i) {
+        int32_t v;
+        asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(flag) : "memory");
+        if (v != 0) {
+            *status = PX_OK;
+            return;
+        }
+        __nanosleep(64);
+    }
+    *status = PX_ERR_TIMEOUT;
+}
+
+}  // namespace
+}  // namespace px
+
+extern "C" px_status px_selftest_wait(const int32_t* d_flag, uint32_t spin_limit, int32_t* d_status, void* stream) {
+    using namespace px;
+    set_error("");
+    if (!d_flag || !d_status) return fail(PX_ERR_INVALID, "px_selftest_wait: null pointer");
+    if (spin_limit < 1 || spin_limit > (1u << 24))
+        return fail(PX_ERR_INVALID, "px_selftest_wait: spin_limit %u outside [1, 2^24]", spin_limit);
+    selftest_wait_kernel<<<1, 1, 0, static_cast<cudaStream_t>(stream)>>>(d_flag, spin_limit, d_status);
+    note_launch();
+    return check_launch("px_selftest_wait");
+}

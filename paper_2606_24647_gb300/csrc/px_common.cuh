@@ -13,6 +13,8 @@
 #include <cstdarg>
 #include <cstdio>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "px.h"
 
 namespace px {
@@ -290,6 +292,15 @@ void set_error(const char* fmt, ...);
 px_status fail(px_status code, const char* fmt, ...);
 px_status check_launch(const char* what);
 void note_launch();  // counts one kernel launch (px_kernel_launches)
+
+// NVTX range around one C-ABI call (host enqueue time), named after the call, for
+// timeline tools; free when no tool is attached.
+struct CallRange {
+    explicit CallRange(const char* name) { nvtxRangePushA(name); }
+    ~CallRange() { nvtxRangePop(); }
+    CallRange(const CallRange&) = delete;
+    CallRange& operator=(const CallRange&) = delete;
+};
 
 inline bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 inline bool valid_type(int32_t t) { return t == PX_I8 || t == PX_I32 || t == PX_I64; }

@@ -82,6 +82,7 @@ size_t px_filter_ws_bytes(int64_t nrows) {
 
 px_status px_filter(const px_col* col, int64_t nrows, const int64_t* d_nrows, int64_t lo, int64_t hi,
                     int32_t* d_sel, int64_t* d_nsel, void* d_ws, size_t ws_bytes, void* stream) {
+    CallRange nvtx_range("px_filter");
     set_error("");
     px_status s = check_col(col, "px_filter col", nrows == 0);
     if (s != PX_OK) return s;
@@ -171,6 +172,7 @@ px_status noalloc_scratch(void** out) {
 extern "C" px_status px_filter_noalloc(const px_col* col, int64_t nrows, const int64_t* d_nrows, int64_t lo,
                                        int64_t hi, int32_t* d_sel, int64_t* d_nsel, int32_t* d_status,
                                        void* stream) {
+    CallRange nvtx_range("px_filter_noalloc");
     set_error("");
     px_status s = check_col(col, "px_filter_noalloc col", nrows == 0);
     if (s != PX_OK) return s;

@@ -439,6 +439,7 @@ size_t px_fragments_ws_bytes(const px_fragment* frags, int32_t nfrags) {
 
 px_status px_fragments_run(const px_fragment* frags, int32_t nfrags, const px_fragments_config* cfg, void* h_plan,
                            size_t plan_bytes, void* d_ws, size_t ws_bytes, void* stream) {
+    CallRange nvtx_range("px_fragments_run");
     set_error("");
     if (nfrags < 0 || (nfrags > 0 && !frags)) return fail(PX_ERR_INVALID, "px_fragments_run: bad fragment list");
     if (nfrags > INT32_MAX / 2) return fail(PX_ERR_UNSUPPORTED, "px_fragments_run: too many fragments");

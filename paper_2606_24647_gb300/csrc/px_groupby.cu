@@ -749,6 +749,7 @@ px_status px_groupby_agg(const px_batch* in, const int32_t* key_cols, int32_t nk
                          int32_t naggs, const int32_t* d_sel, const int64_t* d_nsel, const int64_t* d_seg,
                          int32_t nsegs, const px_key_range* range, int64_t max_groups, const px_batch* out,
                          int32_t* d_out_seg, int64_t* d_ngroups, void* d_ws, size_t ws_bytes, void* stream) {
+    CallRange nvtx_range("px_groupby_agg");
     set_error("");
     px_status s = check_batch(in, "px_groupby_agg in");
     if (s != PX_OK) return s;

@@ -608,6 +608,7 @@ size_t px_join_probe_ws_bytes(int64_t nprobe) {
 
 px_status px_join_build(const px_batch* build, int32_t pk_col, const int64_t* d_seg, int32_t nsegs, int32_t unique,
                         void* d_table, size_t table_bytes, void* d_ws, size_t ws_bytes, void* stream) {
+    CallRange nvtx_range("px_join_build");
     set_error("");
     px_status s = check_batch(build, "px_join_build build");
     if (s != PX_OK) return s;
@@ -650,6 +651,7 @@ px_status px_join_probe(const void* d_table, const px_batch* probe, int32_t fk_c
                         int32_t ncarry, const px_batch* build_payload, const px_batch* out, int32_t* d_probe_row,
                         int32_t* d_build_row, int64_t* d_nout, int64_t* d_out_seg, void* d_ws, size_t ws_bytes,
                         void* stream) {
+    CallRange nvtx_range("px_join_probe");
     set_error("");
     px_status s = check_batch(probe, "px_join_probe probe");
     if (s != PX_OK) return s;

@@ -415,6 +415,7 @@ size_t px_partition_ws_bytes(int64_t nrows, int32_t nparts) {
 px_status px_partition(const px_batch* in, int32_t key_col, const int32_t* d_sel, const int64_t* d_nsel,
                        int32_t nparts, uint64_t seed, const px_batch* out, int64_t* d_offsets, void* d_ws,
                        size_t ws_bytes, void* stream) {
+    CallRange nvtx_range("px_partition");
     set_error("");
     px_status s = check_batch(in, "px_partition in");
     if (s != PX_OK) return s;

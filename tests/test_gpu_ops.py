@@ -361,3 +361,22 @@ def test_groupby_capacity_overflow_reported(px):
     res = px.px_groupby_agg([dev(k)], [0], [(px.PX_COUNT, None, None)], max_groups=100, ws=ws)
     assert ws.status() == px.PX_ERR_CAPACITY
     assert count(res["ngroups"]) == 1000
+
+
+# ------------------------------------------------------- bounded waits -----
+
+def test_bounded_wait_times_out_and_context_stays_usable(px):
+    # a flag nothing sets: the device wait gives up with PX_ERR_TIMEOUT (no hang,
+    # no fault), and the context keeps working afterwards
+    flag = torch.zeros(1, dtype=torch.int32, device="cuda")
+    status = torch.full((1,), -1, dtype=torch.int32, device="cuda")
+    px.px_selftest_wait(flag, 20_000, status)
+    assert count(status) == px.PX_ERR_TIMEOUT
+    flag.fill_(1)
+    px.px_selftest_wait(flag, 20_000, status)
+    assert count(status) == px.PX_OK
+    col = dev(np.arange(1000, dtype=np.int32))
+    sel, nsel = px.px_filter(col, 10, 20)
+    assert count(nsel) == 10
+    with pytest.raises(px.PxError):
+        px.px_selftest_wait(flag, 0, status)
