@@ -472,6 +472,70 @@ def run_fragments(args):
     return 0
 
 
+# ------------------------------------------------ late materialization ----
+LATE_WORKLOAD = ("selective join over a wide fact: 60M-row fact (fk Zipf s=1.1 over 2M pks, amount, price, qty "
+                 "int64, date int32) x the 2M-row dim's rows with attr < 1000 (about 10 %); exchange both into 64 "
+                 "partitions, per-partition join, Partial group-by attr: SUM(amount), SUM(price*qty), COUNT, Final")
+
+
+def run_late_mat(args):
+    """NEXT 4: the same selective join eagerly (exchange fk + amount + price + qty)
+    and late-materialized (exchange fk + row id, gather the payload after the join)."""
+    import torch
+    import paper_2606_24647_gb300 as px
+    from paper_2606_24647_gb300.pipelines import WideJoinPipeline
+
+    torch.cuda.set_device(0)
+    px.load()
+    stream = torch.cuda.current_stream()
+    nf = args.fact_rows or NFACT
+    d = pxdata.wide_at_scale(NDIM, nf, NATTR, build_attr_below=1_000)
+    dd = {k: torch.from_numpy(v).cuda() for k, v in d.items()}
+    torch.cuda.synchronize()
+    out = {}
+    finals = {}
+    for name, late in (("eager", False), ("late", True)):
+        p = WideJoinPipeline(dd, late=late, nparts=NPARTS, nattr_bound=1_000)
+        calls = WideJoinPipeline.CALLS_LATE if late else WideJoinPipeline.CALLS_EAGER
+        r = p.run(stream)
+        torch.cuda.synchronize()
+        if p.ws.status() != px.PX_OK:
+            raise RuntimeError(f"device status in the {name} plan")
+        n = int(r["final"]["ngroups"].item())
+        k = r["final"]["keys"][0][:n].long()
+        o = torch.argsort(k)
+        finals[name] = [k[o]] + [a[:n][o] for a in r["final"]["aggs"]]
+        for _ in range(args.warmup):
+            p.run(stream)
+        evs = [[torch.cuda.Event(enable_timing=True) for _ in range(len(calls) + 1)] for _ in range(args.steps)]
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for s in range(args.steps):
+            p.run(stream, mark=lambda i, s=s: evs[s][i].record(stream))
+        b.record(stream)
+        torch.cuda.synchronize()
+        t = a.elapsed_time(b) / args.steps
+        ops = {c: round(sum(evs[s][i].elapsed_time(evs[s][i + 1]) for s in range(args.steps)) / args.steps, 4)
+               for i, c in enumerate(calls)}
+        nj = int(r["join"]["nout"].item())
+        out[name] = {"ms_per_step": round(t, 4), "fact_rows_per_s": nf / (t / 1000), "operators_ms": ops,
+                     "joined_rows": nj}
+    if not all(torch.equal(x, y) for x, y in zip(finals["eager"], finals["late"])):
+        raise RuntimeError("eager and late-materialized plans disagree")
+    line = {"metric": "fact rows/s, selective wide join: late materialization vs eager exchange",
+            "value": out["late"]["fact_rows_per_s"], "unit": "rows/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": out["late"]["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+            "data": "synthetic (seeded numpy PCG64; TPC-H-like shapes, no TPC-H data)",
+            "config": {"workload": LATE_WORKLOAD, "fact_rows": nf, "dim_rows": NDIM,
+                       "build_rows": int(d["pk_b"].size), "nparts": NPARTS},
+            "late": out["late"], "eager": out["eager"],
+            "speedup_late_vs_eager": out["eager"]["ms_per_step"] / out["late"]["ms_per_step"]}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 # -------------------------------------------------------- serving workload ----
 SERVE_WORKLOAD = ("served fragment queries: 32 resident dimension tables (1K..2M rows, log-spaced; group domains "
                   "log-uniform [4, 1e5]); Poisson arrivals of fragment queries (fact rows log-uniform [1e4, 4e6]) "
@@ -577,7 +641,7 @@ def main(argv=None):
     ap.add_argument("--serve-queries", type=int, default=1000)
     ap.add_argument("--serve-pool", type=int, default=64)
     ap.add_argument("--serve-big", type=int, default=2)
-    ap.add_argument("--workload", default="at-scale", choices=["at-scale", "fragments", "serve"],
+    ap.add_argument("--workload", default="at-scale", choices=["at-scale", "fragments", "serve", "late-mat"],
                     help="at-scale: the exchange-join-aggregate pipeline (default); fragments: the batched fused "
                          "fragments against one-at-a-time calls")
     ap.add_argument("--fragments", type=int, default=FRAG_N)
@@ -590,6 +654,12 @@ def main(argv=None):
         NFACT = args.fact_rows or NFACT
         NDIM = args.dim_rows or NDIM
         WORKLOAD = f"REDUCED for profiling: {NFACT}-row fact x {NDIM}-row dim; otherwise " + WORKLOAD
+    if args.workload == "late-mat":
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable": "the oracle reference arm covers the at-scale "
+                              "workload; the late-materialization plan is compared with the eager plan"}))
+            return 0
+        return run_late_mat(args)
     if args.workload == "serve":
         if args.impl == "reference":
             print(json.dumps({"impl": "reference", "unavailable": "the oracle reference arm covers the at-scale "

@@ -234,6 +234,14 @@ px_status px_join_probe(const void* d_table, const px_batch* probe, int32_t fk_c
                         int64_t* d_nout, int64_t* d_out_seg,
                         void* d_ws, size_t ws_bytes, void* stream);
 
+/* ---- gather (late materialization, Sec. 2.3) ---------------------------- */
+/* out->cols[c][i] = in->cols[c][d_idx[i]] for the positions i < n (n = *d_n when
+ * given, else out->nrows): fetch payload columns by row id after the exchange and
+ * join moved only (key, row id). Types must match per column; an index outside
+ * [0, in->nrows) records PX_ERR_INVALID and that output row is left unwritten. */
+px_status px_gather(const px_batch* in, const int32_t* d_idx, const int64_t* d_n, const px_batch* out,
+                    void* d_ws, size_t ws_bytes, void* stream);
+
 /* ---- hash aggregation (HashAggregation, Sec. 3.2) ----------------------- */
 
 size_t px_groupby_ws_bytes(int64_t nrows, int64_t max_groups);

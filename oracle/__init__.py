@@ -235,6 +235,17 @@ def pipeline_fragment(d: dict, lo: int, hi: int) -> dict:
     return {"sel": sel, "probe_rows": pr, "build_rows": br, "groups": g}
 
 
+def pipeline_wide_join(d: dict) -> dict:
+    """Selective join over a wide fact, aggregated (the answer of both the eager and
+    the late-materialization plans, Sec. 2.3): join fk = pk over the build rows
+    (pk_b, attr_b), group by attr with SUM(amount), SUM(price * qty), COUNT(*).
+    Single mode over unpartitioned rows; groups in ascending attr order."""
+    pr, br, _ = join(d["pk_b"], d["fk"])
+    attr = d["attr_b"][br]
+    return groupby([attr], [(SUM, d["amount"][pr], None), (SUM_MUL, d["price"][pr], d["qty"][pr]),
+                            (COUNT, None, None)])
+
+
 def pipeline_at_scale(d: dict, nparts: int, seed: int = 0) -> dict:
     """Exchange-join-aggregate at scale (Sec. 3.3 exchange feeding per-partition joins
     and Partial aggregation, then a Final merge, Sec. 3.2): partition dim on pk and

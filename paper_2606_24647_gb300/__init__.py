@@ -33,7 +33,7 @@ EXPORTED = [
     "px_partition_ws_bytes", "px_partition",
     "px_join_table_bytes", "px_join_build_ws_bytes", "px_join_build",
     "px_join_probe_ws_bytes", "px_join_probe",
-    "px_groupby_ws_bytes", "px_groupby_agg",
+    "px_groupby_ws_bytes", "px_groupby_agg", "px_gather",
     "px_fragments_plan_bytes", "px_fragments_ws_bytes", "px_fragments_run",
 ]
 PX_FRAG_MAX_COLS, PX_FRAG_MAX_AGGS, PX_FRAG_MAX_GROUPS = 4, 4, 1 << 22
@@ -105,6 +105,7 @@ def _declare(lib):
         "px_groupby_ws_bytes": ([I64, I64], SZ),
         "px_groupby_agg": ([BP, P, I32, AP, I32, P, P, P, I32, ctypes.POINTER(px_key_range), I64, BP, P, P, P,
                             SZ, P], I32),
+        "px_gather": ([BP, P, P, BP, P, SZ, P], I32),
         "px_fragments_plan_bytes": ([I32], SZ),
         "px_fragments_ws_bytes": ([ctypes.POINTER(px_fragment), I32], SZ),
         "px_fragments_run": ([ctypes.POINTER(px_fragment), I32, ctypes.POINTER(px_fragments_config), P, SZ, P, SZ, P],
@@ -438,3 +439,18 @@ class FragmentBatch:
 def px_selftest_wait(flag: torch.Tensor, spin_limit: int, status: torch.Tensor, stream=None) -> None:
     """Bounded device wait on flag (int32[1]) -> status (int32[1]): PX_OK or PX_ERR_TIMEOUT."""
     _check(load().px_selftest_wait(_ptr(flag), int(spin_limit), _ptr(status), _stream(stream)), "px_selftest_wait")
+
+
+def px_gather(cols, idx, *, n=None, d_n=None, out=None, ws=None, stream=None):
+    """out[c][i] = cols[c][idx[i]] for the first n positions (or *d_n) - the gather of
+    late materialization. Returns the output columns."""
+    L = load()
+    cap = idx.numel() if n is None else int(n)
+    dev = idx.device
+    if out is None:
+        out = [torch.empty(max(cap, 1), dtype=c.dtype, device=dev) for c in cols]
+    inb = _Batch(cols, cols[0].numel(), None)
+    outb = _Batch(out, cap)
+    ws = _ws(ws, 256, stream)
+    _check(L.px_gather(inb.ref(), _ptr(idx), _ptr(d_n), outb.ref(), ws.ptr, ws.nbytes, _stream(stream)), "px_gather")
+    return out

@@ -10,6 +10,9 @@ never synchronises with the host).
                        join build and probe -> Partial group-by per partition -> Final
                        merge (the exchange feeding the join and aggregation, Sec. 3.3
                        with the aggregation modes of Sec. 3.2).
+* WideJoinPipeline   - a selective join over a wide fact, eager (exchange every needed
+                       column) or late-materialized (exchange (key, row id), gather the
+                       payload after the join; Sec. 2.3).
 * FragmentSet        - many small filter -> join -> aggregate fragments over resident
                        dimension tables, run as one fused batch (px_fragments_run);
   OneAtATime         - the same fragments one at a time through the unfused calls.
@@ -18,8 +21,8 @@ from __future__ import annotations
 
 import torch
 
-from . import (PX_COUNT, PX_SUM, PX_SUM_MUL, FragmentBatch, Workspace, load, px_filter, px_groupby_agg,
-               px_join_build, px_join_probe, px_partition)
+from . import (PX_COUNT, PX_SUM, PX_SUM_MUL, FragmentBatch, Workspace, load, px_filter, px_gather,
+               px_groupby_agg, px_join_build, px_join_probe, px_partition)
 
 
 def _empty_like_cols(cols, n=None):
@@ -224,3 +227,92 @@ class OneAtATime:
                                              max_groups=ng, d_nrows=j["nout"], key_range=[(0, ng - 1)],
                                              out=self.gout[i], ws=self.ws, stream=stream)
         return self.results
+
+
+class WideJoinPipeline:
+    """Selective join over a wide fact: exchange both sides into nparts partitions,
+    join per partition, Partial group-by attr (SUM(amount), SUM(price*qty), COUNT)
+    per partition, Final merge.
+
+    late=False (eager): the fact exchange moves fk and every column the query needs
+    after the join (amount, price, qty) and the probe carries them.
+    late=True (late materialization, Sec. 2.3): the fact exchange moves only fk and a
+    row id; the probe carries the row id, and px_gather fetches amount, price and
+    qty for the rows that survived the join."""
+
+    CALLS_EAGER = ["px_partition(dim)", "px_partition(fact)", "px_join_build", "px_join_probe",
+                   "px_groupby_agg(partial)", "px_groupby_agg(final)"]
+    CALLS_LATE = ["px_partition(dim)", "px_partition(fact)", "px_join_build", "px_join_probe", "px_gather",
+                  "px_groupby_agg(partial)", "px_groupby_agg(final)"]
+
+    def __init__(self, d: dict, late: bool, nparts: int = 64, seed: int = 0, nattr_bound: int = 1_000):
+        L = load()
+        self.d, self.late, self.nparts, self.seed = d, late, nparts, seed
+        self.attr_range = (0, nattr_bound - 1)
+        nf, nd = d["fk"].numel(), d["pk_b"].numel()
+        dev = d["fk"].device
+        self.rowid = torch.arange(nf, dtype=torch.int32, device=dev) if late else None
+        self.fact = [d["fk"], self.rowid] if late else [d["fk"], d["amount"], d["price"], d["qty"]]
+        self.dim = [d["pk_b"], d["attr_b"]]
+        self.fparts = _empty_like_cols(self.fact)
+        self.dparts = _empty_like_cols(self.dim)
+        self.foff = torch.empty(nparts + 1, dtype=torch.int64, device=dev)
+        self.doff = torch.empty(nparts + 1, dtype=torch.int64, device=dev)
+        self.table = torch.empty(L.px_join_table_bytes(max(nd, 1), nparts), dtype=torch.uint8, device=dev)
+        cap = max(nf, 1)
+        if late:  # probe output: row id, attr; then the gathered payload
+            self.jout = [torch.empty(cap, dtype=torch.int32, device=dev), torch.empty(cap, dtype=torch.int32, device=dev)]
+            self.gout = [torch.empty(cap, dtype=torch.int64, device=dev) for _ in range(3)]
+        else:     # probe output: amount, price, qty, attr
+            self.jout = [torch.empty(cap, dtype=torch.int64, device=dev) for _ in range(3)] + \
+                        [torch.empty(cap, dtype=torch.int32, device=dev)]
+        self.max_partial = min(cap, nparts * nattr_bound)
+        self.max_final = min(cap, nattr_bound)
+        self.pout = [torch.empty(self.max_partial, dtype=torch.int32, device=dev)] + \
+                    [torch.empty(self.max_partial, dtype=torch.int64, device=dev) for _ in range(3)]
+        self.fout = [torch.empty(self.max_final, dtype=torch.int32, device=dev)] + \
+                    [torch.empty(self.max_final, dtype=torch.int64, device=dev) for _ in range(3)]
+        need = max(L.px_partition_ws_bytes(nf, nparts), L.px_partition_ws_bytes(nd, nparts),
+                   L.px_join_build_ws_bytes(nd), L.px_join_probe_ws_bytes(nf),
+                   L.px_groupby_ws_bytes(nf, self.max_partial))
+        self.ws = Workspace(need)
+
+    def run(self, stream=None, mark=None) -> dict:
+        P, ws = self.nparts, self.ws
+        rng = [self.attr_range]
+        mark = mark or (lambda i: None)
+        k = 0
+        mark(k)
+        px_partition(self.dim, 0, P, self.seed, out=self.dparts, offsets=self.doff, ws=ws, stream=stream)
+        k += 1
+        mark(k)
+        px_partition(self.fact, 0, P, self.seed, out=self.fparts, offsets=self.foff, ws=ws, stream=stream)
+        k += 1
+        mark(k)
+        px_join_build(self.dparts, 0, seg=self.doff, unique=True, table=self.table, ws=ws, stream=stream)
+        k += 1
+        mark(k)
+        carry = [1] if self.late else [1, 2, 3]
+        j = px_join_probe(self.table, self.fparts, 0, seg=self.foff, carry=carry, payload=[self.dparts[1]],
+                          out=self.jout, out_cap=self.jout[0].numel(), out_seg=True, ws=ws, stream=stream)
+        k += 1
+        mark(k)
+        if self.late:
+            px_gather([self.d["amount"], self.d["price"], self.d["qty"]], self.jout[0], d_n=j["nout"],
+                      out=self.gout, ws=ws, stream=stream)
+            k += 1
+            mark(k)
+            cols = self.gout + [self.jout[1]]
+        else:
+            cols = self.jout
+        part = px_groupby_agg(cols, [3], [(PX_SUM, 0, None), (PX_SUM_MUL, 1, 2), (PX_COUNT, None, None)],
+                              max_groups=self.max_partial, seg=j["out_seg"], d_nrows=j["nout"], key_range=rng,
+                              out=self.pout, ws=ws, stream=stream)
+        k += 1
+        mark(k)
+        final = px_groupby_agg(self.pout, [0], [(PX_SUM, 1, None), (PX_SUM, 2, None), (PX_SUM, 3, None)],
+                               max_groups=self.max_final, d_nrows=part["ngroups"], key_range=rng, out=self.fout,
+                               ws=ws, stream=stream)
+        k += 1
+        mark(k)
+        return {"join": j, "partial": part, "final": final}

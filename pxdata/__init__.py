@@ -100,6 +100,25 @@ def plain_at_scale(ndim: int = 2_000_000, nfact: int = 60_000_000, nattr: int = 
     return {"pk": pk, "attr": attr, "fk": fk, "amount": amount, "date": date}
 
 
+def wide_at_scale(ndim: int = 2_000_000, nfact: int = 60_000_000, nattr: int = 10_000, build_attr_below: int = 1_000,
+                  seed: int = 6) -> dict:
+    """Selective join over a wide fact (the late-materialization workload).
+
+    The at-scale pair (same recipe, this seed) plus fact price int64 U[100, 10^7]
+    (scale 2) and qty int64 U[1, 50], drawn after it. The build side is the
+    dimension rows with attr < build_attr_below (about 10 % of them), so only the
+    fact rows whose key names one of those survive the join.
+    """
+    d = plain_at_scale(ndim, nfact, nattr, seed=seed)
+    g = _rng(seed + 1000)
+    d["price"] = g.integers(100, 10**7, size=nfact, dtype=np.int64, endpoint=True)
+    d["qty"] = g.integers(1, 50, size=nfact, dtype=np.int64, endpoint=True)
+    keep = d["attr"] < build_attr_below
+    d["pk_b"] = d["pk"][keep]
+    d["attr_b"] = d["attr"][keep]
+    return d
+
+
 def _log_uniform_int(g: np.random.Generator, lo: int, hi: int, size: int) -> np.ndarray:
     return np.floor(np.exp(g.uniform(np.log(lo), np.log(hi), size=size))).astype(np.int64)
 
