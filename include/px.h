@@ -275,6 +275,32 @@ px_status px_groupby_agg(const px_batch* in, const int32_t* key_cols, int32_t nk
                          int64_t max_groups, const px_batch* out, int32_t* d_out_seg,
                          int64_t* d_ngroups, void* d_ws, size_t ws_bytes, void* stream);
 
+/* Streaming aggregation (HashAggregation's Partial mode flushing its groups when
+ * they pass a size threshold, and a Final that keeps merging them, Sec. 3.2): the
+ * same call as px_groupby_agg plus flags.
+ *   PX_AGG_STREAM      the call starts a stream of calls that share d_ws and the
+ *                      outputs: the aggregation mode then depends on the key
+ *                      statistic and max_groups only, not on the row count, so
+ *                      every call of the stream keeps its groups in one place.
+ *   PX_AGG_ACCUMULATE  continue the stream: add this call's rows into the groups
+ *                      the earlier calls left in d_ws and the outputs (same keys,
+ *                      aggregates, statistic, segments count, max_groups and
+ *                      workspace) instead of starting empty. *d_ngroups and the
+ *                      first *d_ngroups output rows then cover every call so far.
+ * flags = 0 is px_groupby_agg. Emitting a Partial stream's groups into a Final
+ * stream is another px_groupby_agg_stream over the Partial outputs with
+ * d_nrows = its group count; the Partial stream then restarts without
+ * PX_AGG_ACCUMULATE. */
+#define PX_AGG_ACCUMULATE 1
+#define PX_AGG_STREAM 2
+px_status px_groupby_agg_stream(const px_batch* in, const int32_t* key_cols, int32_t nkeys,
+                                const px_agg* aggs, int32_t naggs,
+                                const int32_t* d_sel, const int64_t* d_nsel,
+                                const int64_t* d_seg, int32_t nsegs, const px_key_range* range,
+                                int64_t max_groups, const px_batch* out, int32_t* d_out_seg,
+                                int64_t* d_ngroups, int32_t flags, void* d_ws, size_t ws_bytes,
+                                void* stream);
+
 /* ---- batched fused fragments: filter -> probe -> aggregate ------------- */
 /* The paper runs many small plan fragments whose vectors are too small to fill a
  * GPU (Sec. 3.3.2; batch-size sensitivity, Sec. 3.4). This entry point runs a

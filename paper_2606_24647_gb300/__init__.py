@@ -26,6 +26,7 @@ STATUS_NAMES = {0: "PX_OK", 1: "PX_ERR_INVALID", 2: "PX_ERR_CAPACITY", 3: "PX_ER
                 4: "PX_ERR_TABLE_FULL", 5: "PX_ERR_TIMEOUT", 6: "PX_ERR_CUDA", 7: "PX_ERR_UNSUPPORTED"}
 PX_I8, PX_I32, PX_I64 = 1, 4, 8
 PX_COUNT, PX_SUM, PX_SUM_MUL = 0, 1, 2
+PX_AGG_ACCUMULATE, PX_AGG_STREAM = 1, 2
 
 EXPORTED = [
     "px_ws_init", "px_stream_status", "px_last_error", "px_kernel_launches", "px_selftest_wait",
@@ -33,7 +34,7 @@ EXPORTED = [
     "px_partition_ws_bytes", "px_partition",
     "px_join_table_bytes", "px_join_build_ws_bytes", "px_join_build",
     "px_join_probe_ws_bytes", "px_join_probe",
-    "px_groupby_ws_bytes", "px_groupby_agg", "px_gather",
+    "px_groupby_ws_bytes", "px_groupby_agg", "px_groupby_agg_stream", "px_gather",
     "px_fragments_plan_bytes", "px_fragments_ws_bytes", "px_fragments_run",
 ]
 PX_FRAG_MAX_COLS, PX_FRAG_MAX_AGGS, PX_FRAG_MAX_GROUPS = 4, 4, 1 << 22
@@ -105,6 +106,8 @@ def _declare(lib):
         "px_groupby_ws_bytes": ([I64, I64], SZ),
         "px_groupby_agg": ([BP, P, I32, AP, I32, P, P, P, I32, ctypes.POINTER(px_key_range), I64, BP, P, P, P,
                             SZ, P], I32),
+        "px_groupby_agg_stream": ([BP, P, I32, AP, I32, P, P, P, I32, ctypes.POINTER(px_key_range), I64, BP, P, P,
+                                   I32, P, SZ, P], I32),
         "px_gather": ([BP, P, P, BP, P, SZ, P], I32),
         "px_fragments_plan_bytes": ([I32], SZ),
         "px_fragments_ws_bytes": ([ctypes.POINTER(px_fragment), I32], SZ),
@@ -326,7 +329,7 @@ def px_join_probe(table, cols, fk_col: int, *, sel=None, nsel=None, seg=None, d_
 
 
 def px_groupby_agg(cols, key_cols, aggs, *, max_groups: int, sel=None, nsel=None, seg=None, d_nrows=None,
-                   key_range=None, out=None, ws=None, stream=None):
+                   key_range=None, out=None, ws=None, stream=None, flags: int = 0, ngroups=None, out_seg=None):
     """GROUP BY key_cols computing aggs = [(op, a, b), ...] (HashAggregation, Sec. 3.2).
 
     key_range: optional [(lo, hi), ...] per key column, a statistic of where the keys
@@ -347,19 +350,22 @@ def px_groupby_agg(cols, key_cols, aggs, *, max_groups: int, sel=None, nsel=None
     aarr = (px_agg * max(1, len(aggs)))(*[px_agg(op, a if a is not None else -1, b if b is not None else -1)
                                           for op, a, b in aggs])
     res = {"keys": out[:len(key_cols)], "aggs": out[len(key_cols):],
-           "ngroups": torch.empty(1, dtype=torch.int64, device=dev)}
+           "ngroups": ngroups if ngroups is not None else torch.empty(1, dtype=torch.int64, device=dev)}
     if nsegs > 0:
-        res["seg"] = torch.empty(max_groups, dtype=torch.int32, device=dev)
+        res["seg"] = out_seg if out_seg is not None else torch.empty(max_groups, dtype=torch.int32, device=dev)
     rng = None
     if key_range is not None:
         rng = px_key_range()
         for k, (lo, hi) in enumerate(key_range):
             rng.lo[k], rng.hi[k] = int(lo), int(hi)
     ws = _ws(ws, L.px_groupby_ws_bytes(n, max_groups), stream)
-    _check(L.px_groupby_agg(inb.ref(), karr, len(key_cols), aarr, len(aggs), _sel_ptr(sel), _ptr(nsel), _ptr(seg),
-                            nsegs, ctypes.byref(rng) if rng is not None else None, max_groups, outb.ref(),
-                            _ptr(res.get("seg")), _ptr(res["ngroups"]), ws.ptr, ws.nbytes, _stream(stream)),
-           "px_groupby_agg")
+    args = (inb.ref(), karr, len(key_cols), aarr, len(aggs), _sel_ptr(sel), _ptr(nsel), _ptr(seg), nsegs,
+            ctypes.byref(rng) if rng is not None else None, max_groups, outb.ref(), _ptr(res.get("seg")),
+            _ptr(res["ngroups"]))
+    if flags:
+        _check(L.px_groupby_agg_stream(*args, int(flags), ws.ptr, ws.nbytes, _stream(stream)), "px_groupby_agg_stream")
+    else:
+        _check(L.px_groupby_agg(*args, ws.ptr, ws.nbytes, _stream(stream)), "px_groupby_agg")
     return res
 
 

@@ -122,8 +122,14 @@ __device__ int32_t global_group(const GTable& g, const Spec& sp, uint64_t code, 
                 const int32_t gi = idx < static_cast<unsigned long long>(max_groups) ? static_cast<int32_t>(idx) : -1;
                 g.key[s] = code;
                 g.gidx[s] = gi;
-                if (gi >= 0) write_group(sp, code, gi, out_seg);
-                else set_status(status, PX_ERR_CAPACITY);
+                if (gi >= 0) {
+                    write_group(sp, code, gi, out_seg);
+                    // The row's accumulators start at zero (an output row may hold an
+                    // earlier call's value when calls accumulate into one table).
+                    for (int a = 0; a < sp.naggs; ++a) sp.agg_out[a][gi] = 0;
+                } else {
+                    set_status(status, PX_ERR_CAPACITY);
+                }
                 __threadfence();
                 atomicExch(&g.state[s], 2u);
                 return gi;
@@ -745,12 +751,16 @@ size_t px_groupby_ws_bytes(int64_t nrows, int64_t max_groups) {
     return ws_layout(max_groups).total;
 }
 
-px_status px_groupby_agg(const px_batch* in, const int32_t* key_cols, int32_t nkeys, const px_agg* aggs,
-                         int32_t naggs, const int32_t* d_sel, const int64_t* d_nsel, const int64_t* d_seg,
-                         int32_t nsegs, const px_key_range* range, int64_t max_groups, const px_batch* out,
-                         int32_t* d_out_seg, int64_t* d_ngroups, void* d_ws, size_t ws_bytes, void* stream) {
-    CallRange nvtx_range("px_groupby_agg");
+static px_status groupby_impl(const px_batch* in, const int32_t* key_cols, int32_t nkeys, const px_agg* aggs,
+                              int32_t naggs, const int32_t* d_sel, const int64_t* d_nsel, const int64_t* d_seg,
+                              int32_t nsegs, const px_key_range* range, int64_t max_groups, const px_batch* out,
+                              int32_t* d_out_seg, int64_t* d_ngroups, int32_t flags, void* d_ws, size_t ws_bytes,
+                              void* stream) {
     set_error("");
+    if (flags & ~(PX_AGG_ACCUMULATE | PX_AGG_STREAM))
+        return fail(PX_ERR_INVALID, "px_groupby_agg_stream: unknown flags 0x%x", flags);
+    const bool accumulate = (flags & PX_AGG_ACCUMULATE) != 0;
+    const bool streaming = accumulate || (flags & PX_AGG_STREAM) != 0;
     px_status s = check_batch(in, "px_groupby_agg in");
     if (s != PX_OK) return s;
     if (nkeys < 1 || nkeys > PX_MAX_KEYS || !key_cols)
@@ -853,8 +863,11 @@ px_status px_groupby_agg(const px_batch* in, const int32_t* key_cols, int32_t nk
                              (sp.count_agg < 0 ? (D + 31) / 32 * 4 : 0);
             per_rep = align_up(per_rep, 8);
             const uint64_t E = static_cast<uint64_t>(nsegs > 0 ? nsegs : 1) * D;
+            // A stream of calls keeps its groups in one place: the choice then depends
+            // on the statistic and max_groups only, never on the row count.
             const bool few_rows =
-                cdiv(in->nrows, std::max<int64_t>(kTile, 4 * static_cast<int64_t>(D))) < num_sms();
+                streaming ? per_rep > kSmemBudget
+                          : cdiv(in->nrows, std::max<int64_t>(kTile, 4 * static_cast<int64_t>(D))) < num_sms();
             if (E <= static_cast<uint64_t>(max_groups) && few_rows) {
                 sp.dense = 1;
                 sp.direct = 1;
@@ -890,8 +903,7 @@ px_status px_groupby_agg(const px_batch* in, const int32_t* key_cols, int32_t nk
     g.key = reinterpret_cast<unsigned long long*>(ws + L.key);
     g.gidx = reinterpret_cast<int32_t*>(ws + L.gidx);
     g.mask = G - 1;
-    cudaMemsetAsync(ws + L.counter, 0, 256 + 4ull * G, st);
-    for (int a = 0; a < naggs; ++a) cudaMemsetAsync(sp.agg_out[a], 0, 8ull * max_groups, st);
+    if (!accumulate) cudaMemsetAsync(ws + L.counter, 0, 256 + 4ull * G, st);
     // Dense global result when the whole (segment, key) space fits max_groups.
     sp.dglobal = 0;
     if (sp.dense) {
@@ -901,8 +913,10 @@ px_status px_groupby_agg(const px_batch* in, const int32_t* key_cols, int32_t nk
             sp.E = E;
             sp.dg_acc = reinterpret_cast<unsigned long long*>(ws + L.dg_acc);
             sp.dg_occ = reinterpret_cast<uint8_t*>(ws + L.dg_occ);
-            cudaMemsetAsync(sp.dg_acc, 0, 8ull * naggs * E, st);
-            if (sp.count_agg < 0) cudaMemsetAsync(sp.dg_occ, 0, E, st);
+            if (!accumulate) {
+                cudaMemsetAsync(sp.dg_acc, 0, 8ull * naggs * E, st);
+                if (sp.count_agg < 0) cudaMemsetAsync(sp.dg_occ, 0, E, st);
+            }
         }
     }
     const int64_t ncap = in->nrows;
@@ -932,6 +946,25 @@ px_status px_groupby_agg(const px_batch* in, const int32_t* key_cols, int32_t nk
     }
     cudaMemcpyAsync(d_ngroups, g.ngroups, sizeof(int64_t), cudaMemcpyDeviceToDevice, st);
     return check_launch("px_groupby_agg count");
+}
+
+px_status px_groupby_agg(const px_batch* in, const int32_t* key_cols, int32_t nkeys, const px_agg* aggs,
+                         int32_t naggs, const int32_t* d_sel, const int64_t* d_nsel, const int64_t* d_seg,
+                         int32_t nsegs, const px_key_range* range, int64_t max_groups, const px_batch* out,
+                         int32_t* d_out_seg, int64_t* d_ngroups, void* d_ws, size_t ws_bytes, void* stream) {
+    CallRange nvtx_range("px_groupby_agg");
+    return groupby_impl(in, key_cols, nkeys, aggs, naggs, d_sel, d_nsel, d_seg, nsegs, range, max_groups, out,
+                        d_out_seg, d_ngroups, 0, d_ws, ws_bytes, stream);
+}
+
+px_status px_groupby_agg_stream(const px_batch* in, const int32_t* key_cols, int32_t nkeys, const px_agg* aggs,
+                                int32_t naggs, const int32_t* d_sel, const int64_t* d_nsel, const int64_t* d_seg,
+                                int32_t nsegs, const px_key_range* range, int64_t max_groups, const px_batch* out,
+                                int32_t* d_out_seg, int64_t* d_ngroups, int32_t flags, void* d_ws, size_t ws_bytes,
+                                void* stream) {
+    CallRange nvtx_range("px_groupby_agg_stream");
+    return groupby_impl(in, key_cols, nkeys, aggs, naggs, d_sel, d_nsel, d_seg, nsegs, range, max_groups, out,
+                        d_out_seg, d_ngroups, flags, d_ws, ws_bytes, stream);
 }
 
 }  // extern "C"

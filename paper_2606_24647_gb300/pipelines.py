@@ -13,6 +13,8 @@ never synchronises with the host).
 * WideJoinPipeline   - a selective join over a wide fact, eager (exchange every needed
                        column) or late-materialized (exchange (key, row id), gather the
                        payload after the join; Sec. 2.3).
+* StreamingAggregation - Partial aggregation over a stream of batches emitting its
+                       groups into a Final aggregation past a size threshold (Sec. 3.2).
 * FragmentSet        - many small filter -> join -> aggregate fragments over resident
                        dimension tables, run as one fused batch (px_fragments_run);
   OneAtATime         - the same fragments one at a time through the unfused calls.
@@ -21,8 +23,8 @@ from __future__ import annotations
 
 import torch
 
-from . import (PX_COUNT, PX_SUM, PX_SUM_MUL, FragmentBatch, Workspace, load, px_filter, px_gather,
-               px_groupby_agg, px_join_build, px_join_probe, px_partition)
+from . import (PX_AGG_ACCUMULATE, PX_AGG_STREAM, PX_COUNT, PX_SUM, PX_SUM_MUL, FragmentBatch, Workspace, load,
+               px_filter, px_gather, px_groupby_agg, px_join_build, px_join_probe, px_partition)
 
 
 def _empty_like_cols(cols, n=None):
@@ -316,3 +318,73 @@ class WideJoinPipeline:
         k += 1
         mark(k)
         return {"join": j, "partial": part, "final": final}
+
+
+class StreamingAggregation:
+    """Partial aggregation over a stream of batches that emits its groups into a
+    Final aggregation whenever they reach `threshold` (HashAggregation's Partial and
+    Final modes, Sec. 3.2), all on one stream; the final result equals one Single
+    aggregation over every batch fed. The size check is asynchronous: the group
+    count of feed k is read (from pinned host memory) before feed k + 2, so the
+    Partial table holds at most threshold + two batches' new groups
+    (max_partial must allow that)."""
+
+    def __init__(self, key_dtype, aggs: list, *, threshold: int, max_partial: int, max_final: int,
+                 key_range=None, device=None):
+        L = load()
+        dev = device or torch.device("cuda", torch.cuda.current_device())
+        self.aggs, self.threshold = aggs, int(threshold)
+        self.max_partial, self.max_final, self.key_range = int(max_partial), int(max_final), key_range
+        na = len(aggs)
+        self.pout = [torch.empty(self.max_partial, dtype=key_dtype, device=dev)] + \
+                    [torch.empty(self.max_partial, dtype=torch.int64, device=dev) for _ in range(na)]
+        self.fout = [torch.empty(self.max_final, dtype=key_dtype, device=dev)] + \
+                    [torch.empty(self.max_final, dtype=torch.int64, device=dev) for _ in range(na)]
+        self.p_ng = torch.zeros(1, dtype=torch.int64, device=dev)
+        self.f_ng = torch.zeros(1, dtype=torch.int64, device=dev)
+        self.ws_p = Workspace(L.px_groupby_ws_bytes(1, self.max_partial), device=dev)
+        self.ws_f = Workspace(L.px_groupby_ws_bytes(1, self.max_final), device=dev)
+        self.host_counts = [torch.zeros(1, dtype=torch.int64).pin_memory() for _ in range(2)]
+        self.events = [None, None]
+        self.partial_fresh = True
+        self.final_fresh = True
+        self.feeds = 0
+        self.emissions = 0
+
+    def feed(self, cols: list, key_col: int, d_nrows=None, stream=None):
+        """Aggregate one batch (cols[key_col] the key) into the Partial stream."""
+        k = self.feeds % 2
+        ev = self.events[k]  # the count copied two feeds ago
+        if ev is not None:
+            ev.synchronize()
+            self.events[k] = None
+            if not self.partial_fresh and int(self.host_counts[k].item()) >= self.threshold:
+                self.emit(stream)
+        px_groupby_agg(cols, [key_col], self.aggs, max_groups=self.max_partial, d_nrows=d_nrows,
+                       key_range=self.key_range, out=self.pout, ws=self.ws_p, stream=stream, ngroups=self.p_ng,
+                       flags=PX_AGG_STREAM if self.partial_fresh else PX_AGG_ACCUMULATE)
+        self.partial_fresh = False
+        s = stream or torch.cuda.current_stream()
+        self.host_counts[k].copy_(self.p_ng, non_blocking=True)
+        e = torch.cuda.Event()
+        e.record(s)
+        self.events[k] = e
+        self.feeds += 1
+
+    def emit(self, stream=None):
+        """Merge the Partial groups into the Final stream and restart the Partial."""
+        if self.partial_fresh:
+            return
+        rng = [self.key_range[0]] if self.key_range else None
+        px_groupby_agg(self.pout, [0], [(PX_SUM, 1 + a, None) for a in range(len(self.aggs))],
+                       max_groups=self.max_final, d_nrows=self.p_ng, key_range=rng, out=self.fout, ws=self.ws_f,
+                       stream=stream, ngroups=self.f_ng,
+                       flags=PX_AGG_STREAM if self.final_fresh else PX_AGG_ACCUMULATE)
+        self.final_fresh = False
+        self.partial_fresh = True
+        self.emissions += 1
+        self.events = [None, None]  # counts of the emitted Partial are stale
+
+    def finish(self, stream=None) -> dict:
+        self.emit(stream)
+        return {"keys": self.fout[:1], "aggs": self.fout[1:], "ngroups": self.f_ng, "emissions": self.emissions}
