@@ -31,7 +31,7 @@ constexpr size_t kStageBudget = 48 * 1024;  // raw tile staging bytes (all colum
 constexpr int kOffRegs = (PX_MAX_PARTS + kThreads - 1) / kThreads;  // partitions per thread, at most
 
 constexpr int kScanThreads = 256;
-constexpr int kScanItems = 8;
+constexpr int kScanItems = 32;  // 8192 counts per scan tile: a short look-back chain
 constexpr int kScanTile = kScanThreads * kScanItems;
 
 struct Cols {
@@ -102,11 +102,22 @@ part_scan_kernel(const int32_t* __restrict__ cnt, int32_t* __restrict__ offs, in
     const int64_t base = tile * kScanTile + static_cast<int64_t>(tid) * kScanItems;
     int32_t v[kScanItems];
     int32_t sum = 0;
+    const bool full = base + kScanItems <= total;  // a thread's run is 128-byte aligned
+    if (full) {
 #pragma unroll
-    for (int k = 0; k < kScanItems; ++k) {
-        v[k] = base + k < total ? cnt[base + k] : 0;
-        sum += v[k];
+        for (int k = 0; k < kScanItems; k += 4) {
+            const int4 x = *reinterpret_cast<const int4*>(cnt + base + k);
+            v[k] = x.x;
+            v[k + 1] = x.y;
+            v[k + 2] = x.z;
+            v[k + 3] = x.w;
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < kScanItems; ++k) v[k] = base + k < total ? cnt[base + k] : 0;
     }
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) sum += v[k];
     const int32_t incl = warp_incl_scan(sum);
     if (lane == 31) s_warp[warp] = incl;
     __syncthreads();
@@ -123,14 +134,29 @@ part_scan_kernel(const int32_t* __restrict__ cnt, int32_t* __restrict__ offs, in
     }
     __syncthreads();
     int64_t run = s_excl + s_warp[warp] + incl - sum;
+    // Partition starts inside this thread's run: the multiples of ntiles there.
+    int64_t next_q = (base + ntiles - 1) / ntiles;  // first partition starting at or after base
+    int64_t next_e = next_q * ntiles;
+    int32_t o[kScanItems];
 #pragma unroll
     for (int k = 0; k < kScanItems; ++k) {
         const int64_t e = base + k;
-        if (e < total) {
-            offs[e] = static_cast<int32_t>(run);
-            if (e % ntiles == 0) d_offsets[e / ntiles] = run;
+        o[k] = static_cast<int32_t>(run);
+        if (e < total && e == next_e) {
+            d_offsets[next_q] = run;
+            ++next_q;
+            next_e += ntiles;
         }
         run += v[k];
+    }
+    if (full) {
+#pragma unroll
+        for (int k = 0; k < kScanItems; k += 4)
+            *reinterpret_cast<int4*>(offs + base + k) = make_int4(o[k], o[k + 1], o[k + 2], o[k + 3]);
+    } else {
+#pragma unroll
+        for (int k = 0; k < kScanItems; ++k)
+            if (base + k < total) offs[base + k] = o[k];
     }
 }
 
