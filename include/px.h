@@ -275,6 +275,27 @@ px_status px_groupby_agg(const px_batch* in, const int32_t* key_cols, int32_t nk
                          int64_t max_groups, const px_batch* out, int32_t* d_out_seg,
                          int64_t* d_ngroups, void* d_ws, size_t ws_bytes, void* stream);
 
+/* Fused join probe + aggregation (the probe pipeline feeding HashAggregation in
+ * Single, or per segment Partial, mode; Sec. 3.1, Sec. 3.2): the same groups as
+ * px_join_probe (unique table, carrying the probe columns the aggregates read and
+ * the build column `group` as payload) followed by px_groupby_agg grouping by that
+ * payload column with key statistic [group_lo, group_hi], but without writing
+ * the join output. aggs index the columns of `probe`; out = the group key column
+ * (group->type) then naggs PX_I64 columns, capacity max_groups; with nsegs > 0
+ * (must equal the table's) groups are per segment and d_out_seg receives each
+ * group's segment. The statistic must be small enough for dense aggregation
+ * (PX_ERR_UNSUPPORTED otherwise); group keys outside it are still aggregated
+ * exactly. A multi-map table records PX_ERR_UNSUPPORTED. Groups come in an
+ * unspecified order. */
+size_t px_join_probe_agg_ws_bytes(int64_t nprobe, int64_t max_groups);
+px_status px_join_probe_agg(const void* d_table, const px_batch* probe, int32_t fk_col,
+                            const int32_t* d_sel, const int64_t* d_nsel,
+                            const int64_t* d_seg, int32_t nsegs,
+                            const px_col* group, int64_t nbuild, int64_t group_lo, int64_t group_hi,
+                            const px_agg* aggs, int32_t naggs,
+                            int64_t max_groups, const px_batch* out, int32_t* d_out_seg,
+                            int64_t* d_ngroups, void* d_ws, size_t ws_bytes, void* stream);
+
 /* Streaming aggregation (HashAggregation's Partial mode flushing its groups when
  * they pass a size threshold, and a Final that keeps merging them, Sec. 3.2): the
  * same call as px_groupby_agg plus flags.

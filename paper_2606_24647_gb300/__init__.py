@@ -35,6 +35,7 @@ EXPORTED = [
     "px_join_table_bytes", "px_join_build_ws_bytes", "px_join_build",
     "px_join_probe_ws_bytes", "px_join_probe",
     "px_groupby_ws_bytes", "px_groupby_agg", "px_groupby_agg_stream", "px_gather",
+    "px_join_probe_agg_ws_bytes", "px_join_probe_agg",
     "px_fragments_plan_bytes", "px_fragments_ws_bytes", "px_fragments_run",
 ]
 PX_FRAG_MAX_COLS, PX_FRAG_MAX_AGGS, PX_FRAG_MAX_GROUPS = 4, 4, 1 << 22
@@ -109,6 +110,8 @@ def _declare(lib):
         "px_groupby_agg_stream": ([BP, P, I32, AP, I32, P, P, P, I32, ctypes.POINTER(px_key_range), I64, BP, P, P,
                                    I32, P, SZ, P], I32),
         "px_gather": ([BP, P, P, BP, P, SZ, P], I32),
+        "px_join_probe_agg_ws_bytes": ([I64, I64], SZ),
+        "px_join_probe_agg": ([P, BP, I32, P, P, P, I32, CP, I64, I64, I64, AP, I32, I64, BP, P, P, P, SZ, P], I32),
         "px_fragments_plan_bytes": ([I32], SZ),
         "px_fragments_ws_bytes": ([ctypes.POINTER(px_fragment), I32], SZ),
         "px_fragments_run": ([ctypes.POINTER(px_fragment), I32, ctypes.POINTER(px_fragments_config), P, SZ, P, SZ, P],
@@ -460,3 +463,32 @@ def px_gather(cols, idx, *, n=None, d_n=None, out=None, ws=None, stream=None):
     ws = _ws(ws, 256, stream)
     _check(L.px_gather(inb.ref(), _ptr(idx), _ptr(d_n), outb.ref(), ws.ptr, ws.nbytes, _stream(stream)), "px_gather")
     return out
+
+
+def px_join_probe_agg(table, cols, fk_col: int, group, group_range, aggs, *, max_groups: int, sel=None, nsel=None,
+                      seg=None, d_nrows=None, out=None, ngroups=None, out_seg=None, ws=None, stream=None):
+    """Join probe fused with the aggregation grouping by the build column `group`
+    (values in group_range = (lo, hi)); aggs index the probe columns. Returns a dict
+    like px_groupby_agg's ('keys', 'aggs', 'ngroups', 'seg' when segmented)."""
+    L = load()
+    n = cols[0].numel()
+    dev = cols[0].device
+    nsegs = 0 if seg is None else seg.numel() - 1
+    if out is None:
+        out = [torch.empty(max_groups, dtype=group.dtype, device=dev)] + \
+              [torch.empty(max_groups, dtype=torch.int64, device=dev) for _ in aggs]
+    inb = _Batch(cols, n, d_nrows)
+    outb = _Batch(out, max_groups)
+    aarr = (px_agg * max(1, len(aggs)))(*[px_agg(op, a if a is not None else -1, b if b is not None else -1)
+                                          for op, a, b in aggs])
+    g = _col(group)
+    res = {"keys": out[:1], "aggs": out[1:],
+           "ngroups": ngroups if ngroups is not None else torch.empty(1, dtype=torch.int64, device=dev)}
+    if nsegs > 0:
+        res["seg"] = out_seg if out_seg is not None else torch.empty(max_groups, dtype=torch.int32, device=dev)
+    ws = _ws(ws, L.px_join_probe_agg_ws_bytes(n, max_groups), stream)
+    _check(L.px_join_probe_agg(_ptr(table), inb.ref(), fk_col, _sel_ptr(sel), _ptr(nsel), _ptr(seg), nsegs,
+                               ctypes.byref(g), group.numel(), int(group_range[0]), int(group_range[1]), aarr,
+                               len(aggs), max_groups, outb.ref(), _ptr(res.get("seg")), _ptr(res["ngroups"]),
+                               ws.ptr, ws.nbytes, _stream(stream)), "px_join_probe_agg")
+    return res

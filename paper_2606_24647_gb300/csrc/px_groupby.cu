@@ -24,6 +24,7 @@
 #include <algorithm>
 
 #include "px_common.cuh"
+#include "px_table.cuh"
 
 namespace px {
 namespace {
@@ -66,6 +67,13 @@ struct Spec {
     uint64_t E;                   // entries: max(nsegs, 1) * D
     unsigned long long* dg_acc;   // [naggs][E]
     uint8_t* dg_occ;              // [E] occupancy flags, 1 where the entry has rows (only without COUNT)
+    // fused probe (px_join_probe_agg): the key of position j is group[build row of
+    // fk[j] in segment q of the table], or no group when fk[j] has no match
+    const int64_t* probe_fk;
+    TableView probe_t;
+    const void* group_col;
+    int32_t group_w;
+    int64_t nbuild;
 };
 
 struct GTable {
@@ -334,7 +342,8 @@ __device__ __forceinline__ void load_col(const void* p, int w, const int32_t* ro
 // straight into the dense global array with 64-bit global reductions. Chosen for
 // inputs with few rows per entry, where block arrays would cost more to clear
 // and flush than they save (a Final merge of Partial results, say).
-template <int NA, bool DIRECT>
+// PROBE: the key of each position comes from the fused join probe (see Spec).
+template <int NA, bool DIRECT, bool PROBE>
 __device__ void aggregate_range_dense(const Spec& sp, const Smem& m, const int32_t* __restrict__ sel, int64_t a0,
                                       int64_t a1, int q, const GTable& g, int64_t max_groups, int32_t* out_seg,
                                       int32_t* status) {
@@ -346,20 +355,64 @@ __device__ void aggregate_range_dense(const Spec& sp, const Smem& m, const int32
     uint32_t* const A32 = DIRECT ? nullptr : rep_u32(sp, m, rep);
     uint32_t* const OCC = DIRECT ? nullptr : rep_occ(sp, m, rep);
     const uint64_t ebase = static_cast<uint64_t>(q) * sp.D;
+    SegGeom geo = {};
+    if (PROBE) geo = seg_geom(sp.probe_t, q);
     for (int64_t tb = a0; tb < a1; tb += kTile) {
         int32_t row[kItems];
         uint32_t idx[kItems];
+        int64_t pkey[kItems];  // PROBE: the gathered group key
 #pragma unroll
         for (int i = 0; i < kItems; ++i) {
             const int64_t j = tb + i * kThreads + tid;
             row[i] = j < a1 ? (sel ? sel[j] : static_cast<int32_t>(j)) : -1;
         }
-        {
+        if (PROBE) {
+            // Join probe of every position: its key's home bucket (one sector), a walk
+            // on in the rare case that bucket is full without it, the build row, then
+            // the group key gathered from the build column.
+            int64_t fkv[kItems];
+            const Bucket* bp[kItems];
+            longlong2 k01[kItems], k23[kItems];
+#pragma unroll
+            for (int i = 0; i < kItems; ++i) fkv[i] = row[i] >= 0 ? sp.probe_fk[row[i]] : kEmpty;
+#pragma unroll
+            for (int i = 0; i < kItems; ++i) {
+                bp[i] = sp.probe_t.bk + geo.b0 + home_bucket(static_cast<uint64_t>(fkv[i]), geo.nb);
+                if (fkv[i] != kEmpty) {
+                    k01[i] = *reinterpret_cast<const longlong2*>(&bp[i]->key[0]);
+                    k23[i] = *reinterpret_cast<const longlong2*>(&bp[i]->key[2]);
+                } else {
+                    k01[i] = k23[i] = make_longlong2(kEmpty, kEmpty);
+                }
+            }
+            int32_t brow[kItems];
+#pragma unroll
+            for (int i = 0; i < kItems; ++i) {
+                brow[i] = -1;
+                if (fkv[i] == kEmpty) continue;
+                bool end;
+                int l = bucket_find(k01[i], k23[i], fkv[i], &end);
+                const Bucket* b = bp[i];
+                for (uint32_t round = 1; l < 0 && !end && round < geo.nb; ++round) {
+                    b = b + 1 == sp.probe_t.bk + geo.b0 + geo.nb ? sp.probe_t.bk + geo.b0 : b + 1;
+                    l = bucket_find(*reinterpret_cast<const longlong2*>(&b->key[0]),
+                                    *reinterpret_cast<const longlong2*>(&b->key[2]), fkv[i], &end);
+                }
+                if (l >= 0) brow[i] = b->row[l];
+            }
+#pragma unroll
+            for (int i = 0; i < kItems; ++i) {
+                pkey[i] = brow[i] >= 0 ? load_int(sp.group_col, sp.group_w, brow[i]) : 0;
+                const uint64_t o0 = static_cast<uint64_t>(pkey[i] - sp.lo[0]);
+                idx[i] = brow[i] < 0 ? kIdxNone : (o0 < sp.span[0] ? static_cast<uint32_t>(o0) : kIdxOutside);
+            }
+        } else {
             int64_t k0[kItems], k1[kItems];
             load_col(sp.key_in[0], sp.key_w[0], row, k0);
             if (sp.nkeys > 1) load_col(sp.key_in[1], sp.key_w[1], row, k1);
 #pragma unroll
             for (int i = 0; i < kItems; ++i) {
+                pkey[i] = 0;
                 const uint64_t o0 = static_cast<uint64_t>(k0[i] - sp.lo[0]);
                 const uint64_t o1 = sp.nkeys > 1 ? static_cast<uint64_t>(k1[i] - sp.lo[1]) : 0;
                 idx[i] = row[i] < 0 ? kIdxNone
@@ -453,8 +506,8 @@ __device__ void aggregate_range_dense(const Spec& sp, const Smem& m, const int32
         for (int i = 0; i < kItems; ++i) {
             if (idx[i] != kIdxOutside) continue;
             const int64_t r = row[i];
-            const int64_t k0 = load_int(sp.key_in[0], sp.key_w[0], r);
-            const int64_t k1 = sp.nkeys > 1 ? load_int(sp.key_in[1], sp.key_w[1], r) : 0;
+            const int64_t k0 = PROBE ? pkey[i] : load_int(sp.key_in[0], sp.key_w[0], r);
+            const int64_t k1 = !PROBE && sp.nkeys > 1 ? load_int(sp.key_in[1], sp.key_w[1], r) : 0;
             uint64_t full[PX_MAX_AGGS];
 #pragma unroll
             for (int a = 0; a < NA; ++a) full[a] = static_cast<uint64_t>(v[a][i]);
@@ -545,7 +598,7 @@ __device__ void aggregate_range(const Spec& sp, const Smem& m, const int32_t* __
 // separate kernels so each gets its own register allocation.
 constexpr int kHashed = 0, kDenseBlock = 1, kDenseDirect = 2;
 
-template <int NA, int MODE>
+template <int NA, int MODE, bool PROBE = false>
 __global__ void __launch_bounds__(kThreads)
 groupby_kernel(Spec sp, const int32_t* __restrict__ sel, const int64_t* __restrict__ d_n, int64_t ncap,
                const int64_t* __restrict__ d_seg, GTable g, int64_t max_groups, int32_t* __restrict__ out_seg,
@@ -567,6 +620,15 @@ groupby_kernel(Spec sp, const int32_t* __restrict__ sel, const int64_t* __restri
         __syncthreads();
     }
 
+    if (PROBE) {  // a table this call cannot use: no groups (uniform across the block)
+        const TableHeader* h = sp.probe_t.hdr;
+        const int S = sp.nsegs > 0 ? sp.nsegs : 1;
+        if (h->magic != kMagic || h->nsegs != S || h->unique == 0 || h->nbuild > sp.nbuild) {
+            if (blockIdx.x == 0 && threadIdx.x == 0)
+                set_status(status, h->magic == kMagic && h->unique == 0 ? PX_ERR_UNSUPPORTED : PX_ERR_INVALID);
+            return;
+        }
+    }
     const int64_t n = actual_rows(d_n, ncap);
     const int64_t chunk = cdiv(cdiv(n, gridDim.x), kTile) * kTile;
     const int64_t cb = static_cast<int64_t>(blockIdx.x) * chunk;
@@ -583,10 +645,10 @@ groupby_kernel(Spec sp, const int32_t* __restrict__ sel, const int64_t* __restri
             }
         }
         if (MODE == kDenseDirect) {
-            aggregate_range_dense<NA, true>(sp, m, sel, pos, qend, q, g, max_groups, out_seg, status);
+            aggregate_range_dense<NA, true, PROBE>(sp, m, sel, pos, qend, q, g, max_groups, out_seg, status);
         } else {
             if (MODE == kDenseBlock)
-                aggregate_range_dense<NA, false>(sp, m, sel, pos, qend, q, g, max_groups, out_seg, status);
+                aggregate_range_dense<NA, false, PROBE>(sp, m, sel, pos, qend, q, g, max_groups, out_seg, status);
             else
                 aggregate_range<NA>(sp, m, sel, pos, qend, q, g, max_groups, out_seg, status);
             flush_block_table(sp, m, q, g, max_groups, out_seg, status);
@@ -683,11 +745,11 @@ int num_sms() {
     return n > 0 ? n : 1;
 }
 
-template <int NA, int MODE>
+template <int NA, int MODE, bool PROBE = false>
 px_status launch_mode(const Spec& sp, size_t smem, const int32_t* sel, const int64_t* d_n, int64_t ncap,
                       const int64_t* d_seg, const GTable& g, int64_t max_groups, int32_t* out_seg, int32_t* status,
                       uint32_t hslots, cudaStream_t st) {
-    auto kernel = groupby_kernel<NA, MODE>;
+    auto kernel = groupby_kernel<NA, MODE, PROBE>;
     cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, smem);
@@ -704,10 +766,24 @@ px_status launch_mode(const Spec& sp, size_t smem, const int32_t* sel, const int
     return check_launch("px_groupby_agg");
 }
 
+// Fused probe: dense modes only (the caller guarantees sp.dense).
+template <int NA>
+px_status launch_probe(const Spec& sp, size_t smem, const int32_t* sel, const int64_t* d_n, int64_t ncap,
+                       const int64_t* d_seg, const GTable& g, int64_t max_groups, int32_t* out_seg, int32_t* status,
+                       uint32_t hslots, cudaStream_t st) {
+    if (sp.direct)
+        return launch_mode<NA, kDenseDirect, true>(sp, smem, sel, d_n, ncap, d_seg, g, max_groups, out_seg, status,
+                                                   hslots, st);
+    return launch_mode<NA, kDenseBlock, true>(sp, smem, sel, d_n, ncap, d_seg, g, max_groups, out_seg, status, hslots,
+                                              st);
+}
+
 template <int NA>
 px_status launch(const Spec& sp, size_t smem, const int32_t* sel, const int64_t* d_n, int64_t ncap,
                  const int64_t* d_seg, const GTable& g, int64_t max_groups, int32_t* out_seg, int32_t* status,
                  uint32_t hslots, cudaStream_t st) {
+    if (sp.probe_fk)
+        return launch_probe<NA>(sp, smem, sel, d_n, ncap, d_seg, g, max_groups, out_seg, status, hslots, st);
     if (sp.direct)
         return launch_mode<NA, kDenseDirect>(sp, smem, sel, d_n, ncap, d_seg, g, max_groups, out_seg, status, hslots,
                                              st);
@@ -751,11 +827,20 @@ size_t px_groupby_ws_bytes(int64_t nrows, int64_t max_groups) {
     return ws_layout(max_groups).total;
 }
 
+// The fused join probe of px_join_probe_agg: the key of a position is the group
+// column at the build row its fk matches in the table.
+struct ProbeSrc {
+    const void* table;
+    int32_t fk_col;
+    const px_col* group;
+    int64_t nbuild;
+};
+
 static px_status groupby_impl(const px_batch* in, const int32_t* key_cols, int32_t nkeys, const px_agg* aggs,
                               int32_t naggs, const int32_t* d_sel, const int64_t* d_nsel, const int64_t* d_seg,
                               int32_t nsegs, const px_key_range* range, int64_t max_groups, const px_batch* out,
                               int32_t* d_out_seg, int64_t* d_ngroups, int32_t flags, void* d_ws, size_t ws_bytes,
-                              void* stream) {
+                              void* stream, const ProbeSrc* probe = nullptr) {
     set_error("");
     if (flags & ~(PX_AGG_ACCUMULATE | PX_AGG_STREAM))
         return fail(PX_ERR_INVALID, "px_groupby_agg_stream: unknown flags 0x%x", flags);
@@ -786,9 +871,9 @@ static px_status groupby_impl(const px_batch* in, const int32_t* key_cols, int32
     sp.nkeys = nkeys;
     sp.keybits = 0;
     for (int k = 0; k < nkeys; ++k) {
-        if (key_cols[k] < 0 || key_cols[k] >= in->ncols)
+        if (!probe && (key_cols[k] < 0 || key_cols[k] >= in->ncols))
             return fail(PX_ERR_INVALID, "px_groupby_agg: key column %d out of range", key_cols[k]);
-        const px_col& c = in->cols[key_cols[k]];
+        const px_col& c = probe ? *probe->group : in->cols[key_cols[k]];
         if (out->cols[k].type != c.type)
             return fail(PX_ERR_INVALID, "px_groupby_agg: out key column %d type differs from input key", k);
         sp.key_w[k] = c.type;
@@ -890,6 +975,16 @@ static px_status groupby_impl(const px_batch* in, const int32_t* key_cols, int32
             }
         }
     }
+    if (probe) {
+        if (!sp.dense)
+            return fail(PX_ERR_UNSUPPORTED,
+                        "px_join_probe_agg: needs a group key range small enough for dense aggregation");
+        sp.probe_fk = static_cast<const int64_t*>(in->cols[probe->fk_col].data);
+        sp.probe_t = table_view(const_cast<void*>(probe->table), nsegs > 0 ? nsegs : 1);
+        sp.group_col = probe->group->data;
+        sp.group_w = probe->group->type;
+        sp.nbuild = probe->nbuild;
+    }
     const uint32_t hslots = hash_slots(naggs);
     if (!sp.dense) smem = static_cast<size_t>(hslots) * (12 + 8 * static_cast<size_t>(naggs));
 
@@ -965,6 +1060,33 @@ px_status px_groupby_agg_stream(const px_batch* in, const int32_t* key_cols, int
     CallRange nvtx_range("px_groupby_agg_stream");
     return groupby_impl(in, key_cols, nkeys, aggs, naggs, d_sel, d_nsel, d_seg, nsegs, range, max_groups, out,
                         d_out_seg, d_ngroups, flags, d_ws, ws_bytes, stream);
+}
+
+size_t px_join_probe_agg_ws_bytes(int64_t nprobe, int64_t max_groups) { return px_groupby_ws_bytes(nprobe, max_groups); }
+
+px_status px_join_probe_agg(const void* d_table, const px_batch* probe, int32_t fk_col, const int32_t* d_sel,
+                            const int64_t* d_nsel, const int64_t* d_seg, int32_t nsegs, const px_col* group,
+                            int64_t nbuild, int64_t group_lo, int64_t group_hi, const px_agg* aggs, int32_t naggs,
+                            int64_t max_groups, const px_batch* out, int32_t* d_out_seg, int64_t* d_ngroups,
+                            void* d_ws, size_t ws_bytes, void* stream) {
+    CallRange nvtx_range("px_join_probe_agg");
+    set_error("");
+    px_status s = check_batch(probe, "px_join_probe_agg probe");
+    if (s != PX_OK) return s;
+    if (!d_table || !aligned16(d_table)) return fail(PX_ERR_INVALID, "px_join_probe_agg: null or misaligned table");
+    if (fk_col < 0 || fk_col >= probe->ncols || probe->cols[fk_col].type != PX_I64)
+        return fail(PX_ERR_INVALID, "px_join_probe_agg: fk_col must name a PX_I64 probe column");
+    if (!group || nbuild < 0) return fail(PX_ERR_INVALID, "px_join_probe_agg: group column");
+    s = check_col(group, "px_join_probe_agg group", nbuild == 0);
+    if (s != PX_OK) return s;
+    if (group_hi < group_lo) return fail(PX_ERR_INVALID, "px_join_probe_agg: empty group range");
+    px_key_range r = {};
+    r.lo[0] = group_lo;
+    r.hi[0] = group_hi;
+    const int32_t key0 = 0;
+    const ProbeSrc ps = {d_table, fk_col, group, nbuild};
+    return groupby_impl(probe, &key0, 1, aggs, naggs, d_sel, d_nsel, d_seg, nsegs, &r, max_groups, out, d_out_seg,
+                        d_ngroups, 0, d_ws, ws_bytes, stream, &ps);
 }
 
 }  // extern "C"

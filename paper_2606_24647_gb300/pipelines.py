@@ -24,7 +24,7 @@ from __future__ import annotations
 import torch
 
 from . import (PX_AGG_ACCUMULATE, PX_AGG_STREAM, PX_COUNT, PX_SUM, PX_SUM_MUL, FragmentBatch, Workspace, load,
-               px_filter, px_gather, px_groupby_agg, px_join_build, px_join_probe, px_partition)
+               px_filter, px_gather, px_groupby_agg, px_join_build, px_join_probe, px_join_probe_agg, px_partition)
 
 
 def _empty_like_cols(cols, n=None):
@@ -108,10 +108,14 @@ class AtScalePipeline:
 
     CALLS = ["px_partition(dim)", "px_partition(fact)", "px_join_build", "px_join_probe",
              "px_groupby_agg(partial)", "px_groupby_agg(final)"]
+    CALLS_FUSED = ["px_partition(dim)", "px_partition(fact)", "px_join_build", "px_join_probe_agg(partial)",
+                   "px_groupby_agg(final)"]
 
-    def __init__(self, d: dict, nparts: int = 64, seed: int = 0, nattr_bound: int = 10_000, attr_range="auto"):
+    def __init__(self, d: dict, nparts: int = 64, seed: int = 0, nattr_bound: int = 10_000, attr_range="auto",
+                 fused: bool = False):
         L = load()
         self.d = d
+        self.fused = fused  # probe + Partial group-by in one call (px_join_probe_agg)
         self.nparts, self.seed = nparts, seed
         # catalog statistic of dim.attr (speed only); "auto": the attribute's domain [0, nattr_bound)
         self.attr_range = (0, nattr_bound - 1) if attr_range == "auto" else attr_range
@@ -134,10 +138,12 @@ class AtScalePipeline:
                     [torch.empty(self.max_final, dtype=torch.int64, device=dev) for _ in range(2)]
         need = max(L.px_partition_ws_bytes(nf, nparts), L.px_partition_ws_bytes(nd, nparts),
                    L.px_join_build_ws_bytes(nd), L.px_join_probe_ws_bytes(nf),
-                   L.px_groupby_ws_bytes(nf, self.max_partial))
+                   L.px_groupby_ws_bytes(nf, self.max_partial), L.px_join_probe_agg_ws_bytes(nf, self.max_partial))
         self.ws = Workspace(need)
 
     def run(self, stream=None, mark=None) -> dict:
+        if self.fused:
+            return self._run_fused(stream, mark)
         """One pass of the pipeline. mark(i), if given, is called before call i and
         after the last one (i = 0..6), e.g. to record CUDA events between the calls."""
         P, ws = self.nparts, self.ws
@@ -161,6 +167,29 @@ class AtScalePipeline:
                                d_nrows=part["ngroups"], key_range=rng, out=self.fout, ws=ws, stream=stream)
         mark(6)
         return {"dim_offsets": self.doff, "fact_offsets": self.foff, "join": j, "partial": part, "final": final}
+
+    def _run_fused(self, stream=None, mark=None) -> dict:
+        """The same pipeline with the probe and the Partial group-by fused
+        (px_join_probe_agg): the joined rows are never written."""
+        P, ws = self.nparts, self.ws
+        lo, hi = self.attr_range
+        mark = mark or (lambda i: None)
+        mark(0)
+        px_partition(self.dim, 0, P, self.seed, out=self.dparts, offsets=self.doff, ws=ws, stream=stream)
+        mark(1)
+        px_partition(self.fact, 0, P, self.seed, out=self.fparts, offsets=self.foff, ws=ws, stream=stream)
+        mark(2)
+        px_join_build(self.dparts, 0, seg=self.doff, unique=True, table=self.table, ws=ws, stream=stream)
+        mark(3)
+        part = px_join_probe_agg(self.table, self.fparts, 0, self.dparts[1], (lo, hi),
+                                 [(PX_SUM, 1, None), (PX_COUNT, None, None)], max_groups=self.max_partial,
+                                 seg=self.foff, out=self.pout, ws=ws, stream=stream)
+        mark(4)
+        rng = [self.attr_range]
+        final = px_groupby_agg(self.pout, [0], [(PX_SUM, 1, None), (PX_SUM, 2, None)], max_groups=self.max_final,
+                               d_nrows=part["ngroups"], key_range=rng, out=self.fout, ws=ws, stream=stream)
+        mark(5)
+        return {"dim_offsets": self.doff, "fact_offsets": self.foff, "partial": part, "final": final}
 
 
 class FragmentSet:
