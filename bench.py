@@ -306,13 +306,44 @@ def run_px(args):
         gbs = ab[op] / s / 1e9
         operators[op] = {"ms": round(per_op_ms[op], 4), "rows_per_s": rows[op] / s, "alg_bytes": ab[op],
                          "GBps": round(gbs, 1), "hbm_frac": round(gbs / peak, 4)}
+    # The dominant kernel of the step is part_scatter_kernel (the largest share of
+    # the ncu launch list); it runs inside the fact-side px_partition call, which is
+    # timed as a whole (hist + scan + scatter).
     dom = "px_partition(fact)"
     traffic, _ = ncu_traffic("paper_2606_24647_gb300/csrc/px_partition.cu")
     dom_gbs = ab[dom] / (per_op_ms[dom] / 1000) / 1e9
     roofline = {"bound": "hbm", "achieved": round(dom_gbs, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(dom_gbs / peak, 4), "traffic": traffic,
-                "kernel": "px_partition on the 60M-row fact (hist + scan + scatter kernels, one C-ABI call)",
+                "kernel": "px_partition on the 60M-row fact (hist + scan + scatter kernels, one C-ABI call); "
+                          "part_scatter_kernel is the step's largest kernel",
                 "alg_bytes_per_launch": ab[dom], "peak_kind": f"{peak_kind} HBM copy bandwidth (burst)"}
+
+    # ---- the same pipeline with the probe and Partial aggregation fused ----
+    fpipe = AtScalePipeline(dd, nparts=NPARTS, nattr_bound=NATTR, fused=True)
+    fr = fpipe.run(stream)
+    torch.cuda.synchronize()
+    if fpipe.ws.status() != px.PX_OK:
+        raise RuntimeError("device status set in the fused pipeline")
+    nfin = int(fr["final"]["ngroups"].item())
+    if nfin != int(fin["ngroups"].item()) or not all(
+            torch.equal(torch.sort(x[:nfin])[0], torch.sort(y[:nfin])[0])
+            for x, y in zip(fr["final"]["aggs"] + fr["final"]["keys"], fin["aggs"] + fin["keys"])):
+        raise RuntimeError("fused and unfused pipelines disagree")
+    for _ in range(args.warmup):
+        fpipe.run(stream)
+    fcalls = AtScalePipeline.CALLS_FUSED
+    fev = [[torch.cuda.Event(enable_timing=True) for _ in range(len(fcalls) + 1)] for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    for k in range(args.steps):
+        fpipe.run(stream, mark=lambda i, k=k: fev[k][i].record(stream))
+    torch.cuda.synchronize()
+    f_ms = sum(fev[k][0].elapsed_time(fev[k][-1]) for k in range(args.steps)) / args.steps
+    f_max_s = reduce_max(f_ms / 1000.0)
+    fused = {"value": whole_job_rate(NFACT, world, f_max_s), "unit": "rows/s", "ms_per_step": round(f_ms, 4),
+             "operators_ms": {c: round(sum(fev[k][i].elapsed_time(fev[k][i + 1]) for k in range(args.steps)) /
+                                       args.steps, 4) for i, c in enumerate(fcalls)},
+             "note": "px_join_probe + px_groupby_agg(partial) replaced by px_join_probe_agg (join output never "
+                     "written); same final groups (checked)"}
 
     # ---- end to end through the same public calls, host buffers in and out ----
     e2e_steps = max(3, min(20, args.steps // 10))
@@ -362,7 +393,7 @@ def run_px(args):
                        "attr_values": NATTR, "zipf_s": 1.1, "per_gpu_fact_rows": NFACT,
                        "l2": "inputs larger than L2 (1.22 GB of fact+dim columns per step vs 129 MB L2)",
                        "parallelism": f"replicas x{world} (independent seeded shards)"},
-            "operators": operators, "roofline": roofline, "cpu_baseline": cpu,
+            "operators": operators, "roofline": roofline, "fused_probe_partial": fused, "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": "rows/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "steps": e2e_steps},
             "gpu_launches": launches, "clocks": clk}
