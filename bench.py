@@ -346,37 +346,61 @@ def run_px(args):
                      "written); same final groups (checked)"}
 
     # ---- end to end through the same public calls, host buffers in and out ----
+    # Every step copies its five input columns from pinned host memory and reads
+    # its final groups back. Two device input sets and a copy stream let step k+1's
+    # upload run while step k computes (the copies, ~210 GB/s host-to-device, take
+    # longer than the compute), so a step costs max(copy, compute), not the sum.
     e2e_steps = max(3, min(20, args.steps // 10))
-    out_host = {"keys": torch.empty(pipe.max_final, dtype=torch.int32).pin_memory(),
-                "sum": torch.empty(pipe.max_final, dtype=torch.int64).pin_memory(),
-                "cnt": torch.empty(pipe.max_final, dtype=torch.int64).pin_memory(),
-                "n": torch.empty(1, dtype=torch.int64).pin_memory()}
+    dd2 = {k: torch.empty_like(v) for k, v in dd.items()}
+    pipes = [pipe, AtScalePipeline(dd2, nparts=NPARTS, nattr_bound=NATTR)]
+    dsets = [dd, dd2]
+    outs = [{"keys": torch.empty(pipe.max_final, dtype=torch.int32).pin_memory(),
+             "sum": torch.empty(pipe.max_final, dtype=torch.int64).pin_memory(),
+             "cnt": torch.empty(pipe.max_final, dtype=torch.int64).pin_memory(),
+             "n": torch.empty(1, dtype=torch.int64).pin_memory()} for _ in range(2)]
     h2d = sum(v.numel() * v.element_size() for v in host.values())
-    d2h = sum(v.numel() * v.element_size() for v in out_host.values())
+    d2h = sum(v.numel() * v.element_size() for v in outs[0].values())
+    cstream = torch.cuda.Stream()
+    copied = [torch.cuda.Event() for _ in range(2)]
+    computed = [torch.cuda.Event() for _ in range(2)]
 
-    def e2e_step():
-        for k, v in host.items():
-            dd[k].copy_(v, non_blocking=True)
-        _, f = step()
-        out_host["keys"].copy_(f["keys"][0], non_blocking=True)
-        out_host["sum"].copy_(f["aggs"][0], non_blocking=True)
-        out_host["cnt"].copy_(f["aggs"][1], non_blocking=True)
-        out_host["n"].copy_(f["ngroups"], non_blocking=True)
+    def upload(k):
+        b = k % 2
+        if k >= 2:
+            cstream.wait_event(computed[b])  # step k-2 is done with this input set
+        with torch.cuda.stream(cstream):
+            for name, v in host.items():
+                dsets[b][name].copy_(v, non_blocking=True)
+        copied[b].record(cstream)
 
-    e2e_step()
+    def e2e_run(nsteps):
+        upload(0)
+        for k in range(nsteps):
+            if k + 1 < nsteps:
+                upload(k + 1)
+            b = k % 2
+            stream.wait_event(copied[b])
+            f = pipes[b].run(stream)["final"]
+            o = outs[b]
+            o["keys"].copy_(f["keys"][0], non_blocking=True)
+            o["sum"].copy_(f["aggs"][0], non_blocking=True)
+            o["cnt"].copy_(f["aggs"][1], non_blocking=True)
+            o["n"].copy_(f["ngroups"], non_blocking=True)
+            computed[b].record(stream)
+
+    e2e_run(2)
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
-    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    a.record(stream)
-    for _ in range(e2e_steps):
-        e2e_step()
-    b.record(stream)
+    t0 = time.perf_counter()
+    e2e_run(e2e_steps)
     torch.cuda.synchronize()
-    e2e_s = reduce_max(a.elapsed_time(b) / 1000.0)
+    e2e_s = reduce_max(time.perf_counter() - t0)
     e2e_value = whole_job_rate(NFACT * e2e_steps, world, e2e_s)
-    if pipe.ws.status(stream) != px.PX_OK:
+    if pipe.ws.status(stream) != px.PX_OK or pipes[1].ws.status(stream) != px.PX_OK:
         raise RuntimeError("device status set during the end-to-end run")
+    if int(outs[0]["n"].item()) != int(fin["ngroups"].item()):
+        raise RuntimeError("end-to-end result differs")
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -395,7 +419,8 @@ def run_px(args):
                        "parallelism": f"replicas x{world} (independent seeded shards)"},
             "operators": operators, "roofline": roofline, "fused_probe_partial": fused, "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": "rows/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                    "steps": e2e_steps},
+                    "steps": e2e_steps, "clock": "host wall clock around the synchronised run",
+                    "overlap": "step k+1's host-to-device upload runs on a copy stream during step k's compute"},
             "gpu_launches": launches, "clocks": clk}
     if rank == 0:
         print(json.dumps(line), flush=True)
