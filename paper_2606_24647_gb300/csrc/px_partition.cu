@@ -301,18 +301,28 @@ part_scatter_kernel(Cols cols, int32_t key_col, const int32_t* __restrict__ sel,
         posv[i] = base + __popc(peers & lt);
     }
     __syncthreads();
-    // Per partition: exclusive scan over warps (in place) and the tile's count.
-    for (int q = tid; q < static_cast<int>(nparts); q += kThreads) {
-        int32_t run = 0;
-        for (int w = 0; w < kWarps; ++w) {
-            const int32_t c = s_whist[w * np1 + q];
-            s_whist[w * np1 + q] = run;
-            run += c;
+    // Warp 0, 32 partitions at a time: per partition the exclusive scan over the
+    // warps' counters (in place) gives each warp's start inside the partition's run,
+    // and a warp scan of the partitions' tile counts gives each run's start in the
+    // tile (one barrier instead of a block-wide scan).
+    if (warp == 0) {
+        int32_t carry = 0;
+        for (int base = 0; base < static_cast<int>(nparts); base += 32) {
+            const int q = base + lane;
+            int32_t run = 0;
+            if (q < static_cast<int>(nparts)) {
+                for (int w = 0; w < kWarps; ++w) {
+                    const int32_t c = s_whist[w * np1 + q];
+                    s_whist[w * np1 + q] = run;
+                    run += c;
+                }
+            }
+            const int32_t incl = warp_incl_scan(run);
+            if (q < static_cast<int>(nparts)) s_tstart[q] = carry + incl - run;
+            carry += __shfl_sync(FULL, incl, 31);
         }
-        s_tstart[q] = run;
     }
     __syncthreads();
-    block_excl_scan_smem(s_tstart, static_cast<int>(nparts), s_warp);
 #pragma unroll
     for (int r = 0; r < kOffRegs; ++r) {
         const int q = tid + r * kThreads;
