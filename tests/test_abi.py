@@ -126,3 +126,56 @@ def test_host_checks(lib):
 def pxm_max_parts():
     text = open(os.path.join(ROOT, "include", "px.h")).read()
     return int(re.search(r"#define PX_MAX_PARTS (\d+)", text).group(1))
+
+
+def test_host_checks_of_later_entry_points(lib):
+    import paper_2606_24647_gb300 as pxm
+    ws, wsz = FAKE, 1 << 30
+    # streaming group-by: unknown flag bits
+    g_in = _batch(pxm, [pxm.PX_I32, pxm.PX_I64], 100)
+    g_out = _batch(pxm, [pxm.PX_I32, pxm.PX_I64], 100)
+    keys = (ctypes.c_int32 * 1)(0)
+    aggs = (pxm.px_agg * 1)(pxm.px_agg(pxm.PX_SUM, 1, -1))
+    r = lib.px_groupby_agg_stream(ctypes.byref(g_in), keys, 1, aggs, 1, None, None, None, 0, None, 100,
+                                  ctypes.byref(g_out), None, FAKE, 8, ws, wsz, None)
+    assert r == pxm.PX_ERR_INVALID and "flags" in pxm.last_error()
+    # gather: type mismatch between in and out
+    gi = _batch(pxm, [pxm.PX_I64], 100)
+    go = _batch(pxm, [pxm.PX_I32], 100)
+    assert lib.px_gather(ctypes.byref(gi), FAKE, None, ctypes.byref(go), ws, wsz, None) == pxm.PX_ERR_INVALID
+    # fused probe + aggregation: key column not int64, null table, no dense range
+    p = _batch(pxm, [pxm.PX_I32, pxm.PX_I64], 100)
+    grp = pxm.px_col(pxm.PX_I32, 0, FAKE)
+    pa = (pxm.px_agg * 1)(pxm.px_agg(pxm.PX_COUNT, -1, -1))
+    o = _batch(pxm, [pxm.PX_I32, pxm.PX_I64], 100)
+    r = lib.px_join_probe_agg(FAKE, ctypes.byref(p), 0, None, None, None, 0, ctypes.byref(grp), 10, 0, 9, pa, 1,
+                              100, ctypes.byref(o), None, FAKE, ws, wsz, None)
+    assert r == pxm.PX_ERR_INVALID
+    p = _batch(pxm, [pxm.PX_I64, pxm.PX_I64], 100)
+    r = lib.px_join_probe_agg(None, ctypes.byref(p), 0, None, None, None, 0, ctypes.byref(grp), 10, 0, 9, pa, 1,
+                              100, ctypes.byref(o), None, FAKE, ws, wsz, None)
+    assert r == pxm.PX_ERR_INVALID
+    r = lib.px_join_probe_agg(FAKE, ctypes.byref(p), 0, None, None, None, 0, ctypes.byref(grp), 10, 0, 1 << 40, pa, 1,
+                              100, ctypes.byref(o), None, FAKE, ws, wsz, None)
+    assert r == pxm.PX_ERR_UNSUPPORTED
+    # fragments: bad configuration, plan staging too small, group range over the limit
+    f = (pxm.px_fragment * 1)()
+    f[0].nrows = 10
+    f[0].key = pxm.px_col(pxm.PX_I64, 0, FAKE)
+    f[0].d_table = FAKE
+    f[0].nbuild = 10
+    f[0].group = pxm.px_col(pxm.PX_I32, 0, FAKE)
+    f[0].group_lo, f[0].group_hi = 0, 9
+    f[0].max_groups = 10
+    f[0].d_out_keys = FAKE
+    f[0].d_ngroups = FAKE
+    plan = ctypes.create_string_buffer(lib.px_fragments_plan_bytes(1))
+    cfg = pxm.px_fragments_config(128, 4, 512, 1)
+    assert lib.px_fragments_run(f, 1, ctypes.byref(cfg), plan, len(plan), ws, wsz, None) == pxm.PX_ERR_INVALID
+    assert "configuration" in pxm.last_error()
+    assert lib.px_fragments_run(f, 1, None, plan, 8, ws, wsz, None) == pxm.PX_ERR_INVALID
+    f[0].group_hi = 1 << 23
+    assert lib.px_fragments_run(f, 1, None, plan, len(plan), ws, wsz, None) == pxm.PX_ERR_UNSUPPORTED
+    # bounded-wait self-test: null pointers and a zero limit
+    assert lib.px_selftest_wait(None, 10, FAKE, None) == pxm.PX_ERR_INVALID
+    assert lib.px_selftest_wait(FAKE, 0, FAKE, None) == pxm.PX_ERR_INVALID
