@@ -205,7 +205,9 @@ __device__ __forceinline__ void stage_plain(const T* in, T* staged, const int32_
     }
 }
 
-template <int ITEMS>
+// NBITS: bits of the largest partition id (nparts - 1), so the multi-split below
+// is unrolled: one ballot per id bit, plus one for the valid rows of a ragged tile.
+template <int ITEMS, int NBITS>
 __global__ void __launch_bounds__(kThreads, 3)
 part_scatter_kernel(Cols cols, int32_t key_col, const int32_t* __restrict__ sel,
                     const int64_t* __restrict__ d_nsel, int64_t ncap, uint64_t seed, uint32_t nparts,
@@ -217,11 +219,9 @@ part_scatter_kernel(Cols cols, int32_t key_col, const int32_t* __restrict__ sel,
     const int np1p = (np1 + 3) & ~3;
     unsigned char* stage = smem;                                                   // stage_bytes
     void* sorted = smem + stage_bytes;                                             // T x 8 B
-    uint16_t* s_pid = reinterpret_cast<uint16_t*>(smem + stage_bytes + T * 8);    // T
-    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + stage_bytes + T * 10);     // 16 B
-    int32_t* s_warp = reinterpret_cast<int32_t*>(smem + stage_bytes + T * 10 + 16);  // 33 (+3)
-    int32_t* s_tstart = s_warp + 36;                                               // np1p
-    int32_t* s_delta = s_tstart + np1p;                                            // np1p
+    int32_t* s_dest = reinterpret_cast<int32_t*>(smem + stage_bytes + T * 8);     // T
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + stage_bytes + T * 12);     // 16 B
+    int32_t* s_delta = reinterpret_cast<int32_t*>(smem + stage_bytes + T * 12 + 16);  // np1p
     int32_t* s_whist = s_delta + np1p;                                             // kWarps x np1
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -283,16 +283,19 @@ part_scatter_kernel(Cols cols, int32_t key_col, const int32_t* __restrict__ sel,
         const int lp = local_pos<ITEMS>(warp, i, lane);
         pidv[i] = lp < tile_rows ? part_of(keys[lp], seed, nparts) : nparts;
     }
-    const int nbits = 32 - __clz(static_cast<int>(nparts));
     int32_t* wh = s_whist + warp * np1;
     const uint32_t lt = lanemask_lt();
 #pragma unroll
     for (int i = 0; i < ITEMS; ++i) {
+        // A row past a ragged tile's end has p = nparts and is in no valid row's
+        // peer set; it never updates a counter (it is not its own peers' leader).
         const uint32_t p = pidv[i];
-        uint32_t peers = FULL;
-        for (int b = 0; b < nbits; ++b) {
-            const uint32_t bal = __ballot_sync(FULL, (p >> b) & 1u);
-            peers &= ((p >> b) & 1u) ? bal : ~bal;
+        uint32_t peers = tile_rows == T ? FULL : __ballot_sync(FULL, p < nparts);
+#pragma unroll
+        for (int b = 0; b < NBITS; ++b) {
+            const bool bit = (p >> b) & 1u;
+            const uint32_t bal = __ballot_sync(FULL, bit);
+            peers &= bit ? bal : ~bal;
         }
         const int32_t base = wh[p];
         __syncwarp();
@@ -300,39 +303,43 @@ part_scatter_kernel(Cols cols, int32_t key_col, const int32_t* __restrict__ sel,
         __syncwarp();
         posv[i] = base + __popc(peers & lt);
     }
+#pragma unroll
+    for (int r = 0; r < kOffRegs; ++r) {
+        const int q = tid + r * kThreads;
+        if (q < static_cast<int>(nparts)) s_delta[q] = my_off[r];
+    }
     __syncthreads();
-    // Warp 0, 32 partitions at a time: per partition the exclusive scan over the
-    // warps' counters (in place) gives each warp's start inside the partition's run,
-    // and a warp scan of the partitions' tile counts gives each run's start in the
-    // tile (one barrier instead of a block-wide scan).
+    // Warp 0, 32 partitions at a time: the start of each partition's run in the tile
+    // (warp scan of the partitions' counts) plus each warp's start inside the run
+    // (scan of the warps' counters) turn s_whist[w][q] into the tile position of
+    // warp w's first row of partition q, and s_delta[q] into the shift from a tile
+    // position in partition q's run to its output row.
     if (warp == 0) {
         int32_t carry = 0;
         for (int base = 0; base < static_cast<int>(nparts); base += 32) {
             const int q = base + lane;
             int32_t run = 0;
+            if (q < static_cast<int>(nparts))
+                for (int w = 0; w < kWarps; ++w) run += s_whist[w * np1 + q];
+            const int32_t incl = warp_incl_scan(run);
             if (q < static_cast<int>(nparts)) {
+                int32_t at = carry + incl - run;
+                s_delta[q] -= at;
                 for (int w = 0; w < kWarps; ++w) {
                     const int32_t c = s_whist[w * np1 + q];
-                    s_whist[w * np1 + q] = run;
-                    run += c;
+                    s_whist[w * np1 + q] = at;
+                    at += c;
                 }
             }
-            const int32_t incl = warp_incl_scan(run);
-            if (q < static_cast<int>(nparts)) s_tstart[q] = carry + incl - run;
             carry += __shfl_sync(FULL, incl, 31);
         }
     }
     __syncthreads();
 #pragma unroll
-    for (int r = 0; r < kOffRegs; ++r) {
-        const int q = tid + r * kThreads;
-        if (q < static_cast<int>(nparts)) s_delta[q] = my_off[r] - s_tstart[q];
-    }
-#pragma unroll
     for (int i = 0; i < ITEMS; ++i) {
         if (pidv[i] < nparts) {
-            posv[i] += s_tstart[pidv[i]] + wh[pidv[i]];
-            s_pid[posv[i]] = static_cast<uint16_t>(pidv[i]);
+            posv[i] += wh[pidv[i]];
+            s_dest[posv[i]] = posv[i] + s_delta[pidv[i]];
         }
     }
     __syncthreads();
@@ -340,7 +347,7 @@ part_scatter_kernel(Cols cols, int32_t key_col, const int32_t* __restrict__ sel,
 #pragma unroll
     for (int k = 0; k < ITEMS; ++k) {
         const int jj = tid + k * kThreads;
-        dest[k] = jj < tile_rows ? s_delta[s_pid[jj]] + jj : -1;
+        dest[k] = jj < tile_rows ? s_dest[jj] : -1;
     }
 
     // Column phases, one barrier each: phase k writes column order[k-1] to global
@@ -377,7 +384,7 @@ size_t scatter_smem_bytes(int items, uint32_t stage_bytes, int32_t nparts) {
     const size_t T = static_cast<size_t>(kThreads) * items;
     const size_t np1 = static_cast<size_t>(nparts) + 1;
     const size_t np1p = (np1 + 3) & ~static_cast<size_t>(3);
-    return stage_bytes + T * 10 + 16 + 36 * 4 + np1p * 4 * 2 + kWarps * np1 * 4;
+    return stage_bytes + T * 12 + 16 + np1p * 4 + kWarps * np1 * 4;
 }
 
 // Workspace: count matrix, offset matrix (partition-major, P x tiles int32) and the
@@ -425,11 +432,26 @@ px_status launch_partition(const Cols& cols, int32_t key_col, const int32_t* d_s
     if ((s = check_launch("px_partition scan")) != PX_OK) return s;
 
     const size_t smem = scatter_smem_bytes(ITEMS, stage_bytes, nparts);
-    cudaFuncSetAttribute(part_scatter_kernel<ITEMS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         static_cast<int>(smem));
-    part_scatter_kernel<ITEMS><<<static_cast<unsigned>(ntiles), kThreads, smem, st>>>(
-        cols, key_col, d_sel, d_n, ncap, seed, static_cast<uint32_t>(nparts), ps.offs, ntiles, stage_bytes, row_bytes,
-        status);
+    auto go = [&](auto kern) {
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+        kern<<<static_cast<unsigned>(ntiles), kThreads, smem, st>>>(cols, key_col, d_sel, d_n, ncap, seed,
+                                                                     static_cast<uint32_t>(nparts), ps.offs, ntiles,
+                                                                     stage_bytes, row_bytes, status);
+    };
+    static_assert(PX_MAX_PARTS <= 1024, "partition ids need at most 10 bits");
+    switch (nparts <= 1 ? 0 : 32 - __builtin_clz(static_cast<unsigned>(nparts - 1))) {
+        case 0: go(part_scatter_kernel<ITEMS, 0>); break;
+        case 1: go(part_scatter_kernel<ITEMS, 1>); break;
+        case 2: go(part_scatter_kernel<ITEMS, 2>); break;
+        case 3: go(part_scatter_kernel<ITEMS, 3>); break;
+        case 4: go(part_scatter_kernel<ITEMS, 4>); break;
+        case 5: go(part_scatter_kernel<ITEMS, 5>); break;
+        case 6: go(part_scatter_kernel<ITEMS, 6>); break;
+        case 7: go(part_scatter_kernel<ITEMS, 7>); break;
+        case 8: go(part_scatter_kernel<ITEMS, 8>); break;
+        case 9: go(part_scatter_kernel<ITEMS, 9>); break;
+        default: go(part_scatter_kernel<ITEMS, 10>); break;
+    }
     note_launch();
     return check_launch("px_partition scatter");
 }
