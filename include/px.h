@@ -153,11 +153,11 @@ px_status px_filter(const px_col* col, int64_t nrows, const int64_t* d_nrows,
  * byte, or a serving loop that reserves all memory at start-up and must not call
  * cudaMalloc (which may synchronise the device) while serving. Same arguments and
  * results as px_filter, except that its scratch lives in one static device array
- * of 524,800 bytes inside this library (held by every GPU that loads it until the
+ * of 262,400 bytes inside this library (held by every GPU that loads it until the
  * process exits), so nrows may not exceed PX_FILTER_NOALLOC_MAX_ROWS
  * (PX_ERR_UNSUPPORTED otherwise; use px_filter). It allocates nothing. d_status
- * (nullable, device int32) receives the call's device status word (PX_OK or
- * PX_ERR_TIMEOUT). The first call on each device looks up the array's device
+ * (nullable, device int32) receives the call's device status word (PX_OK: the
+ * filter sets no data-dependent error). The first call on each device looks up the array's device
  * address on that device (cudaGetSymbolAddress) and caches it; make that first
  * call before any stream capture. Every call on a device shares the one array and
  * clears what it uses at its start, so calls whose GPU work may overlap (other

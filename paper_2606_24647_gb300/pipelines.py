@@ -55,16 +55,31 @@ class PlainPipeline:
         need = max(L.px_filter_ws_bytes(n), L.px_partition_ws_bytes(n, nparts), L.px_groupby_ws_bytes(n, max_groups))
         self.ws = Workspace(need)
 
+    CALLS = ["px_filter", "px_partition", "px_groupby_agg"]
+
+    def steps(self, stream=None) -> list:
+        """The pipeline's calls in order, as (name, thunk) pairs; run() calls them all."""
+        res = {}
+
+        def groupby():
+            res["groups"] = px_groupby_agg(
+                self.parts, [4, 5], [(PX_SUM, 1, None), (PX_SUM_MUL, 1, 2), (PX_SUM, 2, None), (PX_COUNT, None, None)],
+                max_groups=self.max_groups, d_nrows=self.nsel, key_range=self.key_range, out=self.gout, ws=self.ws,
+                stream=stream)
+
+        self._res = res
+        return list(zip(self.CALLS, [
+            lambda: px_filter(self.d["date"], self.lo, self.hi, sel=self.sel, nsel=self.nsel, ws=self.ws,
+                              stream=stream),
+            lambda: px_partition(self.cols, 0, self.nparts, self.seed, sel=self.sel, nsel=self.nsel, out=self.parts,
+                                 offsets=self.offsets, ws=self.ws, stream=stream),
+            groupby]))
+
     def run(self, stream=None) -> dict:
-        px_filter(self.d["date"], self.lo, self.hi, sel=self.sel, nsel=self.nsel, ws=self.ws, stream=stream)
-        px_partition(self.cols, 0, self.nparts, self.seed, sel=self.sel, nsel=self.nsel, out=self.parts,
-                     offsets=self.offsets, ws=self.ws, stream=stream)
-        g = px_groupby_agg(self.parts, [4, 5], [(PX_SUM, 1, None), (PX_SUM_MUL, 1, 2), (PX_SUM, 2, None),
-                                                (PX_COUNT, None, None)],
-                           max_groups=self.max_groups, d_nrows=self.nsel, key_range=self.key_range, out=self.gout,
-                           ws=self.ws, stream=stream)
+        for _, f in self.steps(stream):
+            f()
         return {"sel": self.sel, "nsel": self.nsel, "parts": dict(zip(self.NAMES, self.parts)),
-                "offsets": self.offsets, "groups": g}
+                "offsets": self.offsets, "groups": self._res["groups"]}
 
 
 class JoinPipeline:
@@ -91,15 +106,34 @@ class JoinPipeline:
                    L.px_groupby_ws_bytes(nf, max_groups))
         self.ws = Workspace(need)
 
+    CALLS = ["px_filter", "px_join_build", "px_join_probe", "px_groupby_agg"]
+
+    def steps(self, stream=None) -> list:
+        """The pipeline's calls in order, as (name, thunk) pairs; run() calls them all."""
+        res = {}
+
+        def probe():
+            res["join"] = px_join_probe(self.table, self.fact, 0, sel=self.sel, nsel=self.nsel, carry=[1],
+                                        payload=[self.d["attr"]], out=self.jout, out_cap=self.jout[0].numel(),
+                                        ws=self.ws, stream=stream)
+
+        def groupby():
+            res["groups"] = px_groupby_agg(self.jout, [1], [(PX_SUM, 0, None), (PX_COUNT, None, None)],
+                                           max_groups=self.max_groups, d_nrows=res["join"]["nout"],
+                                           key_range=[self.attr_range] if self.attr_range else None, out=self.gout,
+                                           ws=self.ws, stream=stream)
+
+        self._res = res
+        return list(zip(self.CALLS, [
+            lambda: px_filter(self.d["date"], self.lo, self.hi, sel=self.sel, nsel=self.nsel, ws=self.ws,
+                              stream=stream),
+            lambda: px_join_build(self.dim, 0, unique=True, table=self.table, ws=self.ws, stream=stream),
+            probe, groupby]))
+
     def run(self, stream=None) -> dict:
-        px_filter(self.d["date"], self.lo, self.hi, sel=self.sel, nsel=self.nsel, ws=self.ws, stream=stream)
-        px_join_build(self.dim, 0, unique=True, table=self.table, ws=self.ws, stream=stream)
-        j = px_join_probe(self.table, self.fact, 0, sel=self.sel, nsel=self.nsel, carry=[1], payload=[self.d["attr"]],
-                          out=self.jout, out_cap=self.jout[0].numel(), ws=self.ws, stream=stream)
-        g = px_groupby_agg(self.jout, [1], [(PX_SUM, 0, None), (PX_COUNT, None, None)], max_groups=self.max_groups,
-                           d_nrows=j["nout"], key_range=[self.attr_range] if self.attr_range else None,
-                           out=self.gout, ws=self.ws, stream=stream)
-        return {"sel": self.sel, "nsel": self.nsel, "join": j, "groups": g}
+        for _, f in self.steps(stream):
+            f()
+        return {"sel": self.sel, "nsel": self.nsel, "join": self._res["join"], "groups": self._res["groups"]}
 
 
 class AtScalePipeline:

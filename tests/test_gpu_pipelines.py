@@ -127,3 +127,47 @@ def test_at_scale_pipeline_full_size(px):
     # Partial groups sum to the final ones and count every joined row.
     pc = host(r["partial"]["aggs"][1], count(r["partial"]["ngroups"]))
     assert int(pc.sum()) == nf
+
+
+@pytest.mark.parametrize("which", ["plain", "join"])
+def test_pipelines_replayed_from_a_cuda_graph(px, which):
+    # Two copies of the pipeline captured back to back in one CUDA graph (how the
+    # bench streams the small workloads): every replay gives the oracle's result.
+    if which == "plain":
+        ds = [pxdata.plain(200_000, s) for s in (0, 1)]
+        pipes = [PlainPipeline(_to_dev(d), pxdata.CFG1_DATE_LO, pxdata.CFG1_DATE_HI, nparts=8) for d in ds]
+        wants = [oracle.pipeline_plain(d, pxdata.CFG1_DATE_LO, pxdata.CFG1_DATE_HI, 8) for d in ds]
+    else:
+        ds = [pxdata.plain_join(20_000, 600_000, seed=s) for s in (2, 3)]
+        pipes = [JoinPipeline(_to_dev(d), pxdata.CFG2_DATE_LO, pxdata.CFG2_DATE_HI) for d in ds]
+        wants = [oracle.pipeline_join(d, pxdata.CFG2_DATE_LO, pxdata.CFG2_DATE_HI) for d in ds]
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        for p in pipes:
+            p.run(side)
+    torch.cuda.current_stream().wait_stream(side)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        outs = [p.run() for p in pipes]
+    for _ in range(2):
+        for o in outs:  # poison the outputs: the replay must rewrite them
+            for t in o["groups"]["aggs"]:
+                t.fill_(-1)
+        graph.replay()
+        torch.cuda.synchronize()
+        for p, o, w, d in zip(pipes, outs, wants, ds):
+            assert p.ws.status() == px.PX_OK
+            if which == "plain":
+                m = count(o["nsel"])
+                np.testing.assert_array_equal(host(o["sel"], m), w["sel"])
+                np.testing.assert_array_equal(host(o["offsets"]), w["offsets"])
+                for name in PlainPipeline.NAMES:
+                    np.testing.assert_array_equal(host(o["parts"][name], m), w["parts"][name])
+                assert_groups_equal(o["groups"], w["groups"], 2)
+            else:
+                m = count(o["join"]["nout"])
+                assert m == w["probe_rows"].size
+                np.testing.assert_array_equal(host(o["join"]["cols"][1], m), d["attr"][w["build_rows"]])
+                assert_groups_equal(o["groups"], w["groups"], 1)
