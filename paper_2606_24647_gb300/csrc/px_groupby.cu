@@ -260,7 +260,53 @@ __device__ __forceinline__ void clear_block_table(const Spec& sp, const Smem& m)
 __device__ void flush_block_table(const Spec& sp, const Smem& m, int q, const GTable& g, int64_t max_groups,
                                   int32_t* out_seg, int32_t* status) {
     __syncthreads();
-    if (sp.dense) {
+    if (sp.dense && sp.reps >= 8) {
+        // Many replicas: one warp per slot, its lanes over the replicas, then a
+        // shuffle sum (a thread per slot would walk every replica alone while the
+        // rest of the block waits at the barrier).
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        for (uint32_t d = warp; d < sp.D; d += kWarps) {
+            uint64_t v[PX_MAX_AGGS];
+            bool occ = false;
+            for (int a = 0; a < sp.naggs; ++a) v[a] = 0;
+            for (int r = lane; r < sp.reps; r += 32) {
+                uint32_t* LO = rep_lo(sp, m, r);
+                uint32_t* HI = rep_hi(sp, m, r);
+                uint32_t* A32 = rep_u32(sp, m, r);
+                for (int a = 0; a < sp.naggs; ++a) {
+                    if (sp.kind[a] == 0) {
+                        const size_t o = static_cast<size_t>(sp.slot[a]) * sp.D + d;
+                        v[a] += (static_cast<uint64_t>(HI[o]) << 32) | LO[o];
+                        LO[o] = 0;
+                        HI[o] = 0;
+                    } else {
+                        uint32_t* p = &A32[static_cast<size_t>(sp.slot[a]) * sp.D + d];
+                        v[a] += *p;
+                        *p = 0;
+                    }
+                }
+                if (sp.count_agg < 0) occ |= ((rep_occ(sp, m, r)[d / 32] >> (d % 32)) & 1u) != 0;
+            }
+            for (int a = 0; a < sp.naggs; ++a) v[a] = warp_sum(v[a]);
+            occ = __any_sync(FULL, occ);
+            if (sp.count_agg >= 0) occ = v[sp.count_agg] != 0;
+            if (!occ || lane != 0) continue;
+            if (sp.dglobal) {
+                const uint64_t e = static_cast<uint64_t>(q) * sp.D + d;
+                for (int a = 0; a < sp.naggs; ++a)
+                    red_add_global(&sp.dg_acc[a * sp.E + e], static_cast<unsigned long long>(v[a]));
+                if (sp.count_agg < 0) sp.dg_occ[e] = 1;
+                continue;
+            }
+            const int64_t k0 = sp.lo[0] + static_cast<int64_t>(d / sp.span[1]);
+            const int64_t k1 = sp.nkeys > 1 ? sp.lo[1] + static_cast<int64_t>(d % sp.span[1]) : 0;
+            global_add(g, sp, compose(sp, k0, k1, q), v, max_groups, out_seg, status);
+        }
+        __syncthreads();
+        if (sp.count_agg < 0)
+            for (uint32_t i = threadIdx.x; i < sp.reps * m.occ_words; i += kThreads)
+                rep_occ(sp, m, i / m.occ_words)[i % m.occ_words] = 0;
+    } else if (sp.dense) {
         for (uint32_t d = threadIdx.x; d < sp.D; d += kThreads) {
             uint64_t v[PX_MAX_AGGS];
             bool occ = false;
