@@ -20,6 +20,8 @@
 //                partition's run contiguously, so the stores coalesce.
 // The key column is read twice (hist and scatter); every other column once; every
 // column written once.
+#include <type_traits>
+
 #include "px_common.cuh"
 
 namespace px {
@@ -162,7 +164,8 @@ part_scan_kernel(const int32_t* __restrict__ cnt, int32_t* __restrict__ offs, in
 
 // Moves one column's tile from the staging area (tile order) into partition order
 // in buffer `buf` (shared memory).
-template <typename T, int ITEMS>
+// FT: a full tile, where every position holds a row (no per-row checks).
+template <typename T, int ITEMS, bool FT>
 __device__ __forceinline__ void transpose_col(const unsigned char* staged, unsigned char* buf, const int32_t* posv,
                                               const uint32_t* pidv, uint32_t nparts, int warp, int lane) {
     const T* src = reinterpret_cast<const T*>(staged);
@@ -170,22 +173,22 @@ __device__ __forceinline__ void transpose_col(const unsigned char* staged, unsig
     T v[ITEMS];
 #pragma unroll
     for (int i = 0; i < ITEMS; ++i)
-        if (pidv[i] < nparts) v[i] = src[local_pos<ITEMS>(warp, i, lane)];
+        if (FT || pidv[i] < nparts) v[i] = src[local_pos<ITEMS>(warp, i, lane)];
 #pragma unroll
     for (int i = 0; i < ITEMS; ++i)
-        if (pidv[i] < nparts) sorted[posv[i]] = v[i];
+        if (FT || pidv[i] < nparts) sorted[posv[i]] = v[i];
 }
 
 // Writes a partition-ordered column tile to its global rows: dest[k] is the output
 // row of partition-ordered position threadIdx.x + k * kThreads (-1 past the tile),
 // so each partition's run is written contiguously.
-template <typename T, int ITEMS>
+template <typename T, int ITEMS, bool FT>
 __device__ __forceinline__ void store_col(const unsigned char* buf, const int32_t* dest, void* out) {
     const T* sorted = reinterpret_cast<const T*>(buf);
     T* o = static_cast<T*>(out);
 #pragma unroll
     for (int k = 0; k < ITEMS; ++k)
-        if (dest[k] >= 0) o[dest[k]] = sorted[threadIdx.x + k * kThreads];
+        if (FT || dest[k] >= 0) o[dest[k]] = sorted[threadIdx.x + k * kThreads];
 }
 
 template <typename T, int ITEMS>
@@ -272,112 +275,118 @@ part_scatter_kernel(Cols cols, int32_t key_col, const int32_t* __restrict__ sel,
         __syncthreads();
     }
 
-    // Partition of every row, then its stable rank inside the warp's run: the lanes
-    // with the same partition id come from one ballot per id bit (multi-split); a
-    // per-warp counter row carries ranks across the thread's items.
-    const int64_t* keys = reinterpret_cast<const int64_t*>(stage + cols.stage_off[key_col]);
-    uint32_t pidv[ITEMS];
-    int32_t posv[ITEMS];
+    // The rest runs specialised for a full tile (every position a row) or not.
+    auto finish = [&](auto full_tile) {
+        constexpr bool FT = decltype(full_tile)::value;
+        // Partition of every row, then its stable rank inside the warp's run: the lanes
+        // with the same partition id come from one ballot per id bit (multi-split); a
+        // per-warp counter row carries ranks across the thread's items.
+        const int64_t* keys = reinterpret_cast<const int64_t*>(stage + cols.stage_off[key_col]);
+        uint32_t pidv[ITEMS];
+        int32_t posv[ITEMS];
 #pragma unroll
-    for (int i = 0; i < ITEMS; ++i) {
-        const int lp = local_pos<ITEMS>(warp, i, lane);
-        pidv[i] = lp < tile_rows ? part_of(keys[lp], seed, nparts) : nparts;
-    }
-    int32_t* wh = s_whist + warp * np1;
-    const uint32_t lt = lanemask_lt();
-#pragma unroll
-    for (int i = 0; i < ITEMS; ++i) {
-        // A row past a ragged tile's end has p = nparts and is in no valid row's
-        // peer set; it never updates a counter (it is not its own peers' leader).
-        const uint32_t p = pidv[i];
-        uint32_t peers = tile_rows == T ? FULL : __ballot_sync(FULL, p < nparts);
-#pragma unroll
-        for (int b = 0; b < NBITS; ++b) {
-            const bool bit = (p >> b) & 1u;
-            const uint32_t bal = __ballot_sync(FULL, bit);
-            peers &= bit ? bal : ~bal;
+        for (int i = 0; i < ITEMS; ++i) {
+            const int lp = local_pos<ITEMS>(warp, i, lane);
+            pidv[i] = FT || lp < tile_rows ? part_of(keys[lp], seed, nparts) : nparts;
         }
-        const int32_t base = wh[p];
-        __syncwarp();
-        if (lane == __ffs(peers) - 1) wh[p] = base + __popc(peers);
-        __syncwarp();
-        posv[i] = base + __popc(peers & lt);
-    }
+        int32_t* wh = s_whist + warp * np1;
+        const uint32_t lt = lanemask_lt();
 #pragma unroll
-    for (int r = 0; r < kOffRegs; ++r) {
-        const int q = tid + r * kThreads;
-        if (q < static_cast<int>(nparts)) s_delta[q] = my_off[r];
-    }
-    __syncthreads();
-    // Warp 0, 32 partitions at a time: the start of each partition's run in the tile
-    // (warp scan of the partitions' counts) plus each warp's start inside the run
-    // (scan of the warps' counters) turn s_whist[w][q] into the tile position of
-    // warp w's first row of partition q, and s_delta[q] into the shift from a tile
-    // position in partition q's run to its output row.
-    if (warp == 0) {
-        int32_t carry = 0;
-        for (int base = 0; base < static_cast<int>(nparts); base += 32) {
-            const int q = base + lane;
-            int32_t run = 0;
-            if (q < static_cast<int>(nparts))
-                for (int w = 0; w < kWarps; ++w) run += s_whist[w * np1 + q];
-            const int32_t incl = warp_incl_scan(run);
-            if (q < static_cast<int>(nparts)) {
-                int32_t at = carry + incl - run;
-                s_delta[q] -= at;
-                for (int w = 0; w < kWarps; ++w) {
-                    const int32_t c = s_whist[w * np1 + q];
-                    s_whist[w * np1 + q] = at;
-                    at += c;
+        for (int i = 0; i < ITEMS; ++i) {
+            // A row past a ragged tile's end has p = nparts and is in no valid row's
+            // peer set; it never updates a counter (it is not its own peers' leader).
+            const uint32_t p = pidv[i];
+            uint32_t peers = FT ? FULL : __ballot_sync(FULL, p < nparts);
+#pragma unroll
+            for (int b = 0; b < NBITS; ++b) {
+                const bool bit = (p >> b) & 1u;
+                const uint32_t bal = __ballot_sync(FULL, bit);
+                peers &= bit ? bal : ~bal;
+            }
+            const int32_t base = wh[p];
+            __syncwarp();
+            if (lane == __ffs(peers) - 1) wh[p] = base + __popc(peers);
+            __syncwarp();
+            posv[i] = base + __popc(peers & lt);
+        }
+#pragma unroll
+        for (int r = 0; r < kOffRegs; ++r) {
+            const int q = tid + r * kThreads;
+            if (q < static_cast<int>(nparts)) s_delta[q] = my_off[r];
+        }
+        __syncthreads();
+        // Warp 0, 32 partitions at a time: the start of each partition's run in the tile
+        // (warp scan of the partitions' counts) plus each warp's start inside the run
+        // (scan of the warps' counters) turn s_whist[w][q] into the tile position of
+        // warp w's first row of partition q, and s_delta[q] into the shift from a tile
+        // position in partition q's run to its output row.
+        if (warp == 0) {
+            int32_t carry = 0;
+            for (int base = 0; base < static_cast<int>(nparts); base += 32) {
+                const int q = base + lane;
+                int32_t run = 0;
+                if (q < static_cast<int>(nparts))
+                    for (int w = 0; w < kWarps; ++w) run += s_whist[w * np1 + q];
+                const int32_t incl = warp_incl_scan(run);
+                if (q < static_cast<int>(nparts)) {
+                    int32_t at = carry + incl - run;
+                    s_delta[q] -= at;
+                    for (int w = 0; w < kWarps; ++w) {
+                        const int32_t c = s_whist[w * np1 + q];
+                        s_whist[w * np1 + q] = at;
+                        at += c;
+                    }
                 }
-            }
-            carry += __shfl_sync(FULL, incl, 31);
-        }
-    }
-    __syncthreads();
-#pragma unroll
-    for (int i = 0; i < ITEMS; ++i) {
-        if (pidv[i] < nparts) {
-            posv[i] += wh[pidv[i]];
-            s_dest[posv[i]] = posv[i] + s_delta[pidv[i]];
-        }
-    }
-    __syncthreads();
-    int32_t dest[ITEMS];
-#pragma unroll
-    for (int k = 0; k < ITEMS; ++k) {
-        const int jj = tid + k * kThreads;
-        dest[k] = jj < tile_rows ? s_dest[jj] : -1;
-    }
-
-    // Column phases, one barrier each: phase k writes column order[k-1] to global
-    // memory from its partition-ordered buffer while moving column order[k] into
-    // partition order. The first column's buffer is the sorted area; column
-    // order[k]'s is the staging area of column order[k-1], free once that column
-    // was moved and at least as large (decreasing widths).
-    for (int k = 0; k <= cols.ncols; ++k) {
-        if (k > 0) {
-            const int c = cols.order[k - 1];
-            const unsigned char* buf =
-                k == 1 ? static_cast<const unsigned char*>(sorted) : stage + cols.stage_off[cols.order[k - 2]];
-            switch (cols.width[c]) {
-                case 8: store_col<int64_t, ITEMS>(buf, dest, cols.out[c]); break;
-                case 4: store_col<int32_t, ITEMS>(buf, dest, cols.out[c]); break;
-                default: store_col<int8_t, ITEMS>(buf, dest, cols.out[c]); break;
-            }
-        }
-        if (k < cols.ncols) {
-            const int c = cols.order[k];
-            unsigned char* buf = k == 0 ? static_cast<unsigned char*>(sorted) : stage + cols.stage_off[cols.order[k - 1]];
-            const unsigned char* st = stage + cols.stage_off[c];
-            switch (cols.width[c]) {
-                case 8: transpose_col<int64_t, ITEMS>(st, buf, posv, pidv, nparts, warp, lane); break;
-                case 4: transpose_col<int32_t, ITEMS>(st, buf, posv, pidv, nparts, warp, lane); break;
-                default: transpose_col<int8_t, ITEMS>(st, buf, posv, pidv, nparts, warp, lane); break;
+                carry += __shfl_sync(FULL, incl, 31);
             }
         }
         __syncthreads();
-    }
+#pragma unroll
+        for (int i = 0; i < ITEMS; ++i) {
+            if (FT || pidv[i] < nparts) {
+                posv[i] += wh[pidv[i]];
+                s_dest[posv[i]] = posv[i] + s_delta[pidv[i]];
+            }
+        }
+        __syncthreads();
+        int32_t dest[ITEMS];
+#pragma unroll
+        for (int k = 0; k < ITEMS; ++k) {
+            const int jj = tid + k * kThreads;
+            dest[k] = FT || jj < tile_rows ? s_dest[jj] : -1;
+        }
+
+        // Column phases, one barrier each: phase k writes column order[k-1] to global
+        // memory from its partition-ordered buffer while moving column order[k] into
+        // partition order. The first column's buffer is the sorted area; column
+        // order[k]'s is the staging area of column order[k-1], free once that column
+        // was moved and at least as large (decreasing widths).
+        for (int k = 0; k <= cols.ncols; ++k) {
+            if (k > 0) {
+                const int c = cols.order[k - 1];
+                const unsigned char* buf =
+                    k == 1 ? static_cast<const unsigned char*>(sorted) : stage + cols.stage_off[cols.order[k - 2]];
+                switch (cols.width[c]) {
+                    case 8: store_col<int64_t, ITEMS, FT>(buf, dest, cols.out[c]); break;
+                    case 4: store_col<int32_t, ITEMS, FT>(buf, dest, cols.out[c]); break;
+                    default: store_col<int8_t, ITEMS, FT>(buf, dest, cols.out[c]); break;
+                }
+            }
+            if (k < cols.ncols) {
+                const int c = cols.order[k];
+                unsigned char* buf = k == 0 ? static_cast<unsigned char*>(sorted) : stage + cols.stage_off[cols.order[k - 1]];
+                const unsigned char* st = stage + cols.stage_off[c];
+                switch (cols.width[c]) {
+                    case 8: transpose_col<int64_t, ITEMS, FT>(st, buf, posv, pidv, nparts, warp, lane); break;
+                    case 4: transpose_col<int32_t, ITEMS, FT>(st, buf, posv, pidv, nparts, warp, lane); break;
+                    default: transpose_col<int8_t, ITEMS, FT>(st, buf, posv, pidv, nparts, warp, lane); break;
+                }
+            }
+            __syncthreads();
+        }
+    };
+    if (tile_rows == T) finish(std::true_type{});
+    else finish(std::false_type{});
 }
 
 size_t scatter_smem_bytes(int items, uint32_t stage_bytes, int32_t nparts) {
