@@ -42,6 +42,20 @@ def test_filter_device_row_count(px):
         np.testing.assert_array_equal(host(sel, want.size), want)
 
 
+def test_filter_tile_counts_scanned_in_several_rounds(px):
+    # More than 8192 tiles of 2048 rows: the one-block scan of the tile counts
+    # carries its total across rounds; a ragged last tile and a d_nrows cut too.
+    g = pxdata.rng(102)
+    n = 8192 * 2048 * 2 + 12_345
+    col = pxdata.random_column(g, n, np.int8)
+    for lo, hi, cut in [(-20, 90, n), (0, 1, n - 777)]:
+        d_n = dev(np.array([cut], np.int64))
+        sel, nsel = px.px_filter(dev(col), lo, hi, d_nrows=d_n)
+        want = oracle.filter(col[:cut], lo, hi)
+        assert count(nsel) == want.size
+        np.testing.assert_array_equal(host(sel, want.size), want)
+
+
 # ----------------------------------------------------------- partition -----
 
 def _part_cols(g, n):
