@@ -106,6 +106,18 @@ __device__ __forceinline__ T warp_sum(T v) {
     return v;
 }
 
+// Sum mod 2^64 of x over the 32 lanes of a warp (all lanes call it): three 32-bit
+// warp reductions (redux.sync) - the low word as two 16-bit halves, whose sums
+// cannot overflow, and the high word mod 2^32 - instead of a 64-bit shuffle
+// butterfly (five rounds of two shuffles and a 64-bit add).
+__device__ __forceinline__ uint64_t warp_sum_u64(uint64_t x) {
+    const uint32_t lo = static_cast<uint32_t>(x), hi = static_cast<uint32_t>(x >> 32);
+    const uint32_t s0 = __reduce_add_sync(FULL, lo & 0xffffu);
+    const uint32_t s1 = __reduce_add_sync(FULL, lo >> 16);
+    const uint32_t sh = __reduce_add_sync(FULL, hi);
+    return static_cast<uint64_t>(s0) + (static_cast<uint64_t>(s1) << 16) + (static_cast<uint64_t>(sh) << 32);
+}
+
 // In-place exclusive scan of s[0..n) in shared memory by the whole block
 // (n <= 4 * blockDim.x, blockDim.x a multiple of 32, <= 1024). `s_warp` holds 33
 // ints. Returns the total. Contains __syncthreads: call from all threads.

@@ -485,7 +485,8 @@ __device__ void aggregate_range_dense(const Spec& sp, const Smem& m, const int32
             }
         }
         // Hot keys: when lane 0's slot is shared by at least kMajority lanes, those
-        // rows are summed with a butterfly and lane 0 applies them once (many lanes
+        // rows are summed across the warp (COUNT is the peer count; 64-bit sums are
+        // three 32-bit warp reductions) and lane 0 applies them once (many lanes
         // on one address would serialise the shared-memory atomics).
         uint32_t apply[kItems];
 #pragma unroll
@@ -499,7 +500,12 @@ __device__ void aggregate_range_dense(const Spec& sp, const Smem& m, const int32
 #pragma unroll
                 for (int a = 0; a < NA; ++a) {
                     if (a >= sp.naggs) break;
-                    const int64_t x = warp_sum(in ? v[a][i] : int64_t(0));
+                    // The probe-fed kernel keeps the shuffle butterfly: redux.sync's
+                    // longer latency measured slower there.
+                    const int64_t x = PROBE ? warp_sum(in ? v[a][i] : int64_t(0))
+                                    : sp.op[a] == PX_COUNT
+                                          ? static_cast<int64_t>(__popc(mm))
+                                          : static_cast<int64_t>(warp_sum_u64(in ? static_cast<uint64_t>(v[a][i]) : 0));
                     if (lane == 0) v[a][i] = x;
                 }
                 if (in && lane != 0) apply[i] = kIdxNone;
@@ -605,8 +611,8 @@ __device__ void aggregate_range(const Spec& sp, const Smem& m, const int32_t* __
 #pragma unroll
         for (int i = 0; i < kItems; ++i) {
             const bool valid = row[i] >= 0;
-            // Hot keys: lane 0's code shared by >= kMajority lanes is summed with a
-            // butterfly and applied once by lane 0.
+            // Hot keys: lane 0's code shared by >= kMajority lanes is summed across
+            // the warp and applied once by lane 0.
             bool lead = valid;
             const uint64_t c0 = __shfl_sync(FULL, code[i], 0);
             const uint32_t mm = __ballot_sync(FULL, valid && code[i] == c0);
@@ -615,7 +621,9 @@ __device__ void aggregate_range(const Spec& sp, const Smem& m, const int32_t* __
 #pragma unroll
                 for (int a = 0; a < NA; ++a) {
                     if (a >= sp.naggs) break;
-                    const int64_t x = warp_sum(in ? v[a][i] : int64_t(0));
+                    const int64_t x = sp.op[a] == PX_COUNT
+                                          ? static_cast<int64_t>(__popc(mm))
+                                          : static_cast<int64_t>(warp_sum_u64(in ? static_cast<uint64_t>(v[a][i]) : 0));
                     if (lane == 0) v[a][i] = x;
                 }
                 lead = valid && (!in || lane == 0);
