@@ -372,3 +372,72 @@ def test_zipf_head_share():
     H = float(np.sum(np.arange(1, 200_001, dtype=np.float64) ** -1.1))
     p = 1 / H
     assert abs(top - p * 400_000) < 6 * np.sqrt(400_000 * p * (1 - p))
+
+
+# ------------------------------------------------ composed pipelines -----
+
+def _brute_groups(rows):
+    """rows: (group key, tuple of addends); per key the wrapped sums, keys ascending."""
+    acc = {}
+    for k, vals in rows:
+        cur = acc.setdefault(k, [0] * len(vals))
+        for a, x in enumerate(vals):
+            cur[a] = (cur[a] + x) & M64
+    keys = sorted(acc)
+    return keys, [[s64(acc[k][a]) for k in keys] for a in range(len(acc[keys[0]]) if keys else 0)]
+
+
+def _assert_groups(g, keys, sums):
+    assert g["ngroups"] == len(keys)
+    assert g["keys"][0].tolist() == keys
+    for a, col in enumerate(sums):
+        assert g["aggs"][a].tolist() == col
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_fragment_pipeline_brute_force(seed):
+    # Nested loops over (fact row, dim row) straight from the definition: keep
+    # lo <= date < hi, match key = pk, group by the dim row's attr; SUM(price),
+    # SUM(price * qty), COUNT(*) all from the FACT row.
+    d = pxdata.fragment(300, 40, 6, seed=70 + seed)
+    d["date"][:5] = [pxdata.CFG2_DATE_LO - 1, pxdata.CFG2_DATE_LO, pxdata.CFG2_DATE_HI - 1, pxdata.CFG2_DATE_HI, 0]
+    rows = []
+    for i in range(d["key"].size):
+        if not (pxdata.CFG2_DATE_LO <= d["date"][i] < pxdata.CFG2_DATE_HI):
+            continue
+        for j in range(d["pk"].size):
+            if d["pk"][j] == d["key"][i]:
+                p, q = int(d["price"][i]), int(d["qty"][i])
+                rows.append((int(d["attr"][j]), (p, p * q, 1)))
+    keys, sums = _brute_groups(rows)
+    r = oracle.pipeline_fragment(d, pxdata.CFG2_DATE_LO, pxdata.CFG2_DATE_HI)
+    _assert_groups(r["groups"], keys, sums)
+    assert 0 < len(rows) < d["key"].size  # some rows filtered or unmatched, some kept
+
+
+def test_wide_join_pipeline_brute_force():
+    # Build side = the dim rows with attr below the bound; SUM(amount),
+    # SUM(price * qty), COUNT(*) from the fact row, grouped by the build row's attr.
+    d = pxdata.wide_at_scale(200, 3000, nattr=50, build_attr_below=10, seed=9)
+    rows = []
+    for i in range(d["fk"].size):
+        for j in range(d["pk_b"].size):
+            if d["pk_b"][j] == d["fk"][i]:
+                p, q = int(d["price"][i]), int(d["qty"][i])
+                rows.append((int(d["attr_b"][j]), (int(d["amount"][i]), p * q, 1)))
+    keys, sums = _brute_groups(rows)
+    _assert_groups(oracle.pipeline_wide_join(d), keys, sums)
+    assert 0 < len(rows) < d["fk"].size
+
+
+def test_at_scale_final_brute_force():
+    # Final groups of the exchange -> join -> Partial -> Final chain equal a nested
+    # loop over the unpartitioned rows: SUM(amount) and COUNT(*) by the dim attr.
+    d = pxdata.plain_at_scale(150, 2000, nattr=7, seed=11)
+    rows = []
+    for i in range(d["fk"].size):
+        for j in range(d["pk"].size):
+            if d["pk"][j] == d["fk"][i]:
+                rows.append((int(d["attr"][j]), (int(d["amount"][i]), 1)))
+    keys, sums = _brute_groups(rows)
+    _assert_groups(oracle.pipeline_at_scale(d, 8)["final"], keys, sums)
