@@ -179,3 +179,43 @@ def test_host_checks_of_later_entry_points(lib):
     # bounded-wait self-test: null pointers and a zero limit
     assert lib.px_selftest_wait(None, 10, FAKE, None) == pxm.PX_ERR_INVALID
     assert lib.px_selftest_wait(FAKE, 0, FAKE, None) == pxm.PX_ERR_INVALID
+
+
+def test_host_checks_of_join_probe(lib):
+    # Every argument error px_join_probe detects on the host, before any GPU work.
+    import paper_2606_24647_gb300 as pxm
+    ws, wsz = FAKE, 1 << 30
+    I32, I64 = pxm.PX_I32, pxm.PX_I64
+    probe = _batch(pxm, [I64, I64, I32], 100)
+    pay = _batch(pxm, [I32], 50)
+    out = _batch(pxm, [I64, I32], 100)
+    carry = (ctypes.c_int32 * 1)(1)
+
+    def call(table=FAKE, pb=probe, fk=0, sel=None, nsel=None, seg=None, nsegs=0, cr=carry, ncarry=1, pl=pay,
+             ob=out, nout=FAKE, wsb=wsz):
+        return lib.px_join_probe(table, ctypes.byref(pb), fk, sel, nsel, seg, nsegs, cr, ncarry,
+                                 ctypes.byref(pl) if pl is not None else None, ctypes.byref(ob), None, None, nout,
+                                 None, ws, wsb, None)
+
+    cases = [
+        (dict(table=None), pxm.PX_ERR_INVALID, "table"),
+        (dict(table=FAKE + 8), pxm.PX_ERR_INVALID, "misaligned"),
+        (dict(fk=3), pxm.PX_ERR_INVALID, "fk_col"),
+        (dict(fk=2), pxm.PX_ERR_INVALID, "PX_I64"),
+        (dict(sel=FAKE), pxm.PX_ERR_INVALID, "together"),
+        (dict(nsegs=4097, seg=FAKE), pxm.PX_ERR_UNSUPPORTED, "nsegs"),
+        (dict(nsegs=4), pxm.PX_ERR_INVALID, "d_seg"),
+        (dict(seg=FAKE), pxm.PX_ERR_INVALID, "d_seg"),
+        (dict(cr=None), pxm.PX_ERR_INVALID, "carry"),
+        (dict(ncarry=-1), pxm.PX_ERR_INVALID, "carry"),
+        (dict(pl=None), pxm.PX_ERR_INVALID, "columns"),          # out has one column too many
+        (dict(nout=None), pxm.PX_ERR_INVALID, "d_nout"),
+        (dict(cr=(ctypes.c_int32 * 1)(7)), pxm.PX_ERR_INVALID, "out of range"),
+        (dict(cr=(ctypes.c_int32 * 1)(2)), pxm.PX_ERR_INVALID, "type"),          # carried int32 into int64
+        (dict(pl=_batch(pxm, [I64], 50)), pxm.PX_ERR_INVALID, "payload"),       # payload int64 into int32
+        (dict(wsb=16), pxm.PX_ERR_INVALID, "px_join_probe"),
+    ]
+    for kw, want, msg in cases:
+        r = call(**kw)
+        assert r == want, (kw, r, pxm.last_error())
+        assert msg in pxm.last_error(), (kw, pxm.last_error())
