@@ -219,3 +219,47 @@ def test_host_checks_of_join_probe(lib):
         r = call(**kw)
         assert r == want, (kw, r, pxm.last_error())
         assert msg in pxm.last_error(), (kw, pxm.last_error())
+
+
+def test_host_checks_of_groupby(lib):
+    # Every argument error px_groupby_agg detects on the host, before any GPU work.
+    import paper_2606_24647_gb300 as pxm
+    ws, wsz = FAKE, 1 << 30
+    I32, I64 = pxm.PX_I32, pxm.PX_I64
+    gin = _batch(pxm, [I32, I64, I64], 100)
+    gout = _batch(pxm, [I32, I64, I64], 100)
+    one_key = (ctypes.c_int32 * 1)(0)
+
+    def aggs_of(*a):
+        return (pxm.px_agg * len(a))(*[pxm.px_agg(*x) for x in a])
+
+    good = aggs_of((pxm.PX_SUM, 1, -1), (pxm.PX_SUM_MUL, 1, 2))
+
+    def call(keys=one_key, nkeys=1, aggs=good, naggs=2, sel=None, nsel=None, seg=None, nsegs=0, max_groups=100,
+             ob=gout, ngroups=FAKE, inb=gin, wsb=wsz):
+        return lib.px_groupby_agg(ctypes.byref(inb), keys, nkeys, aggs, naggs, sel, nsel, seg, nsegs, None,
+                                  max_groups, ctypes.byref(ob), None, ngroups, ws, wsb, None)
+
+    cases = [
+        (dict(nkeys=0), pxm.PX_ERR_UNSUPPORTED, "nkeys"),
+        (dict(nkeys=3), pxm.PX_ERR_UNSUPPORTED, "nkeys"),
+        (dict(naggs=-1), pxm.PX_ERR_UNSUPPORTED, "naggs"),
+        (dict(nsel=FAKE), pxm.PX_ERR_INVALID, "together"),
+        (dict(nsegs=4097, seg=FAKE), pxm.PX_ERR_UNSUPPORTED, "nsegs"),
+        (dict(nsegs=2), pxm.PX_ERR_INVALID, "d_seg"),
+        (dict(max_groups=0), pxm.PX_ERR_INVALID, "max_groups"),
+        (dict(ngroups=None), pxm.PX_ERR_INVALID, "d_ngroups"),
+        (dict(naggs=1), pxm.PX_ERR_INVALID, "columns"),                       # out holds two aggregates
+        (dict(max_groups=101), pxm.PX_ERR_INVALID, "capacity"),
+        (dict(keys=(ctypes.c_int32 * 1)(5)), pxm.PX_ERR_INVALID, "key column"),
+        (dict(keys=(ctypes.c_int32 * 1)(1)), pxm.PX_ERR_INVALID, "type"),     # int64 key into an int32 column
+        (dict(aggs=aggs_of((9, 1, -1), (pxm.PX_SUM, 1, -1))), pxm.PX_ERR_INVALID, "unknown op"),
+        (dict(aggs=aggs_of((pxm.PX_SUM, 3, -1), (pxm.PX_SUM, 1, -1))), pxm.PX_ERR_INVALID, "column a"),
+        (dict(aggs=aggs_of((pxm.PX_SUM, 1, -1), (pxm.PX_SUM_MUL, 1, 7))), pxm.PX_ERR_INVALID, "column b"),
+        (dict(ob=_batch(pxm, [I32, I64, I32], 100)), pxm.PX_ERR_INVALID, "PX_I64"),
+        (dict(wsb=16), pxm.PX_ERR_INVALID, "px_groupby_agg"),
+    ]
+    for kw, want, msg in cases:
+        r = call(**kw)
+        assert r == want, (kw, r, pxm.last_error())
+        assert msg in pxm.last_error(), (kw, pxm.last_error())
