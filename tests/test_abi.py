@@ -263,3 +263,42 @@ def test_host_checks_of_groupby(lib):
         r = call(**kw)
         assert r == want, (kw, r, pxm.last_error())
         assert msg in pxm.last_error(), (kw, pxm.last_error())
+
+
+def test_host_checks_of_join_build_and_gather(lib):
+    import paper_2606_24647_gb300 as pxm
+    ws, wsz = FAKE, 1 << 30
+    I32, I64 = pxm.PX_I32, pxm.PX_I64
+    b = _batch(pxm, [I64, I32], 100)
+    big = lib.px_join_table_bytes(100, 0)
+
+    def build(bb=b, pk=0, seg=None, nsegs=0, unique=1, table=FAKE, tbytes=1 << 30, wsb=wsz):
+        return lib.px_join_build(ctypes.byref(bb), pk, seg, nsegs, unique, table, tbytes, ws, wsb, None)
+
+    cases = [
+        (dict(pk=2), pxm.PX_ERR_INVALID, "pk_col"),
+        (dict(pk=1), pxm.PX_ERR_INVALID, "PX_I64"),
+        (dict(nsegs=4097, seg=FAKE), pxm.PX_ERR_UNSUPPORTED, "nsegs"),
+        (dict(nsegs=3), pxm.PX_ERR_INVALID, "d_seg"),
+        (dict(seg=FAKE), pxm.PX_ERR_INVALID, "d_seg"),
+        (dict(table=None), pxm.PX_ERR_INVALID, "table"),
+        (dict(table=FAKE + 4), pxm.PX_ERR_INVALID, "misaligned"),
+        (dict(tbytes=big - 1), pxm.PX_ERR_INVALID, "needed"),
+        (dict(wsb=16), pxm.PX_ERR_INVALID, "px_join_build"),
+    ]
+    for kw, want, msg in cases:
+        r = build(**kw)
+        assert r == want, (kw, r, pxm.last_error())
+        assert msg in pxm.last_error(), (kw, pxm.last_error())
+
+    gin = _batch(pxm, [I64, I32], 100)
+
+    def gather(ob, idx=FAKE, wsb=wsz):
+        return lib.px_gather(ctypes.byref(gin), idx, None, ctypes.byref(ob), ws, wsb, None)
+
+    assert gather(_batch(pxm, [I64], 10)) == pxm.PX_ERR_INVALID and "columns" in pxm.last_error()
+    assert gather(_batch(pxm, [I64, I64], 10)) == pxm.PX_ERR_INVALID and "type" in pxm.last_error()
+    assert gather(_batch(pxm, [I64, I32], 10), idx=None) == pxm.PX_ERR_INVALID and "d_idx" in pxm.last_error()
+    assert gather(_batch(pxm, [I64, I32], 10), wsb=16) == pxm.PX_ERR_INVALID and "px_gather" in pxm.last_error()
+    # no output rows: nothing to do, no index array needed, no GPU work
+    assert gather(_batch(pxm, [I64, I32], 0), idx=None) == pxm.PX_OK
