@@ -260,10 +260,14 @@ __device__ __forceinline__ void clear_block_table(const Spec& sp, const Smem& m)
 __device__ void flush_block_table(const Spec& sp, const Smem& m, int q, const GTable& g, int64_t max_groups,
                                   int32_t* out_seg, int32_t* status) {
     __syncthreads();
-    if (sp.dense && sp.reps >= 8) {
-        // Many replicas: one warp per slot, its lanes over the replicas, then a
-        // shuffle sum (a thread per slot would walk every replica alone while the
-        // rest of the block waits at the barrier).
+    // A warp per slot (lanes over the replicas, then a warp sum) when there are few
+    // slots for many replicas: a thread per slot would walk every replica alone
+    // while the rest of the block waits at the barrier. With many slots the thread
+    // per slot keeps every thread busy and wins (a warp sum costs ~12 thread-slot
+    // steps).
+    const bool warp_flush = sp.dense && (sp.D + kWarps - 1) / kWarps * 12 <
+                                            (sp.D + kThreads - 1) / kThreads * static_cast<uint32_t>(sp.reps);
+    if (warp_flush) {
         const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
         for (uint32_t d = warp; d < sp.D; d += kWarps) {
             uint64_t v[PX_MAX_AGGS];
