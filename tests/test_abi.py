@@ -302,3 +302,19 @@ def test_host_checks_of_join_build_and_gather(lib):
     assert gather(_batch(pxm, [I64, I32], 10), wsb=16) == pxm.PX_ERR_INVALID and "px_gather" in pxm.last_error()
     # no output rows: nothing to do, no index array needed, no GPU work
     assert gather(_batch(pxm, [I64, I32], 0), idx=None) == pxm.PX_OK
+
+
+def test_binding_refuses_host_tensors():
+    # No CPU fallback: a column, pointer or batch built from a host tensor raises
+    # before anything reaches the library.
+    import torch
+    import paper_2606_24647_gb300 as pxm
+    host = torch.zeros(16, dtype=torch.int64)
+    with pytest.raises(ValueError):
+        pxm._col(host)
+    with pytest.raises(ValueError):
+        pxm._ptr(host)
+    with pytest.raises(ValueError):
+        pxm._Batch([host])
+    with pytest.raises(TypeError):
+        pxm._col(torch.zeros(16, dtype=torch.float32))
