@@ -45,7 +45,7 @@ WORKLOAD = ("plain at scale: 60M-row fact (fk Zipf s=1.1 over 2M pks, amount int
             "join build+probe, Partial group-by attr per partition, Final merge")
 NFACT, NDIM, NATTR, NPARTS = 60_000_000, 2_000_000, 10_000, 64
 
-# Algorithmic bytes per unit of each call (measurement section).
+# Algorithmic bytes per unit of each call:
 #   partition: read every column + write every column       (fact 20+20 B/row, dim 12+12 B/row)
 #   build:     read the key + write the 2 table slots per row (8 + 32 B/dim row)
 #   probe:     read fk + amount, write amount + attr          (16 + 12 B/fact row)
@@ -184,10 +184,63 @@ def oracle_rate(d: dict, nsample: int) -> tuple[float, str]:
     return nsample / dt, f"first {nsample} fact rows x full {d['pk'].size}-row dim, {dt:.1f} s"
 
 
+def host_cpu() -> dict:
+    """This host's logical core count and CPU model (stated beside every CPU timing)."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.strip().lower().startswith("model name"):
+                model = ln.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if not model:
+        try:
+            with open("/proc/cpuinfo") as f:
+                for ln in f:
+                    if ln.lower().startswith("model name"):
+                        model = ln.split(":", 1)[1].strip()
+                        break
+        except OSError:
+            pass
+    import platform
+    return {"host_cores": os.cpu_count(), "cpu_model": model or platform.machine()}
+
+
+def merge_final(parts: list) -> tuple:
+    """Final groups of per-chunk at-scale answers merged by key (sums mod 2^64)."""
+    keys = np.concatenate([p["final"]["keys"][0] for p in parts])
+    aggs = [np.concatenate([p["final"]["aggs"][a] for p in parts]).view(np.uint64) for a in range(2)]
+    order = np.argsort(keys, kind="stable")
+    keys = keys[order]
+    starts = np.flatnonzero(np.r_[True, keys[1:] != keys[:-1]])
+    return keys[starts], [np.add.reduceat(a[order], starts).view(np.int64) for a in aggs]
+
+
+def oracle_rate_all_cores(d: dict, nsample: int, threads: int) -> tuple[float, str]:
+    """The CPU oracle on all host cores: the first `nsample` fact rows split into one
+    chunk per thread, each chunk through the whole at-scale pipeline with the full
+    dimension (the oracle's C calls release the interpreter lock), then the chunks'
+    Final groups merged by key. A labelled extra beside the single-threaded
+    oracle, which stays the correctness reference."""
+    import oracle
+    from concurrent.futures import ThreadPoolExecutor
+    bounds = np.linspace(0, nsample, threads + 1).astype(np.int64)
+    chunks = [{"pk": d["pk"], "attr": d["attr"], "fk": d["fk"][a:b], "amount": d["amount"][a:b],
+               "date": d["date"][a:b]} for a, b in zip(bounds[:-1], bounds[1:])]
+    t0 = time.perf_counter()
+    with ThreadPoolExecutor(max_workers=threads) as ex:
+        parts = list(ex.map(lambda c: oracle.pipeline_at_scale(c, NPARTS), chunks))
+    merge_final(parts)
+    dt = time.perf_counter() - t0
+    return nsample / dt, f"first {nsample} fact rows in {threads} chunks x full {d['pk'].size}-row dim, {dt:.1f} s"
+
+
 def run_reference(args):
     world, rank, _ = dist_env()
     if rank != 0:
-        return 0
+        return None
     import oracle
     oracle.build()
     d = pxdata.plain_at_scale(NDIM, NFACT, NATTR, seed=shard_seed(0))
@@ -212,13 +265,26 @@ def run_reference(args):
                        "reference": "CPU oracle (plain single-threaded C++: stable-sort partition, sorted-build "
                                     "join, ordered-map group-by), bounded sample per step"},
             "cpu_baseline": {"value": value, "unit": "rows/s", "cores": 1, "kind": "oracle",
-                             "sample": f"per step: {desc.split(',')[0]}"},
+                             "sample": f"per step: {desc.split(',')[0]}", **host_cpu()},
             "e2e": {"value": value, "unit": "rows/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
-    print(json.dumps(line), flush=True)
-    return 0
+    return line
 
 
 # -------------------------------------------------------------------- px ----
+
+def same_final(host_out: dict, fin: dict) -> bool:
+    """The end-to-end run's final groups (copied to pinned host buffers) equal the
+    resident run's: same count, and the same (key, SUM, COUNT) rows in key order."""
+    n = int(host_out["n"].item())
+    if n != int(fin["ngroups"].item()):
+        return False
+    k1 = host_out["keys"][:n].numpy().astype(np.int64)
+    k2 = fin["keys"][0][:n].cpu().numpy().astype(np.int64)
+    o1, o2 = np.argsort(k1, kind="stable"), np.argsort(k2, kind="stable")
+    return (np.array_equal(k1[o1], k2[o2]) and
+            np.array_equal(host_out["sum"][:n].numpy()[o1], fin["aggs"][0][:n].cpu().numpy()[o2]) and
+            np.array_equal(host_out["cnt"][:n].numpy()[o1], fin["aggs"][1][:n].cpu().numpy()[o2]))
+
 
 def run_px(args):
     import torch
@@ -240,7 +306,12 @@ def run_px(args):
     host = {k: torch.from_numpy(v).pin_memory() for k, v in d.items()}
     dd = {k: v.to(dev, non_blocking=True) for k, v in host.items()}
     torch.cuda.synchronize()
-    pipe = AtScalePipeline(dd, nparts=NPARTS, nattr_bound=NATTR)
+    # exchange launch shapes for this GPU and these inputs (cached per GPU)
+    from paper_2606_24647_gb300 import autotune
+    tag = f"{NFACT}x{NDIM}p{NPARTS}"
+    fcfg = autotune.tune_partition([dd["fk"], dd["amount"], dd["date"]], 0, NPARTS, f"fact{tag}")
+    dcfg = autotune.tune_partition([dd["pk"], dd["attr"]], 0, NPARTS, f"dim{tag}")
+    pipe = AtScalePipeline(dd, nparts=NPARTS, nattr_bound=NATTR, fact_config=fcfg, dim_config=dcfg)
     stream = torch.cuda.current_stream()
 
     ops = list(alg_bytes(1, 1, 1).keys())
@@ -319,7 +390,7 @@ def run_px(args):
                 "alg_bytes_per_launch": ab[dom], "peak_kind": f"{peak_kind} HBM copy bandwidth (burst)"}
 
     # ---- the same pipeline with the probe and Partial aggregation fused ----
-    fpipe = AtScalePipeline(dd, nparts=NPARTS, nattr_bound=NATTR, fused=True)
+    fpipe = AtScalePipeline(dd, nparts=NPARTS, nattr_bound=NATTR, fused=True, fact_config=fcfg, dim_config=dcfg)
     fr = fpipe.run(stream)
     torch.cuda.synchronize()
     if fpipe.ws.status() != px.PX_OK:
@@ -352,7 +423,7 @@ def run_px(args):
     # longer than the compute), so a step costs max(copy, compute), not the sum.
     e2e_steps = max(3, min(20, args.steps // 10))
     dd2 = {k: torch.empty_like(v) for k, v in dd.items()}
-    pipes = [pipe, AtScalePipeline(dd2, nparts=NPARTS, nattr_bound=NATTR)]
+    pipes = [pipe, AtScalePipeline(dd2, nparts=NPARTS, nattr_bound=NATTR, fact_config=fcfg, dim_config=dcfg)]
     dsets = [dd, dd2]
     outs = [{"keys": torch.empty(pipe.max_final, dtype=torch.int32).pin_memory(),
              "sum": torch.empty(pipe.max_final, dtype=torch.int64).pin_memory(),
@@ -402,15 +473,20 @@ def run_px(args):
     e2e_value = whole_job_rate(NFACT * e2e_steps, world, e2e_s)
     if pipe.ws.status(stream) != px.PX_OK or pipes[1].ws.status(stream) != px.PX_OK:
         raise RuntimeError("device status set during the end-to-end run")
-    if int(outs[0]["n"].item()) != int(fin["ngroups"].item()):
+    if not same_final(outs[0], fin):
         raise RuntimeError("end-to-end result differs")
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
         oracle.build()
+        hc = host_cpu()
         rate, desc = oracle_rate(d, min(NFACT, args.cpu_sample))
-        cpu = {"value": rate, "unit": "rows/s", "cores": 1, "kind": "oracle", "sample": desc}
+        cpu = {"value": rate, "unit": "rows/s", "cores": 1, "kind": "oracle", "sample": desc, **hc}
+        if hc["host_cores"] and hc["host_cores"] > 1:
+            arate, adesc = oracle_rate_all_cores(d, min(NFACT, args.cpu_sample), hc["host_cores"])
+            cpu["all_cores"] = {"value": arate, "unit": "rows/s", "cores": hc["host_cores"],
+                                "kind": "oracle, per-thread chunks + merge of the Final groups", "sample": adesc}
 
     line = {"metric": METRIC, "value": value, "unit": "rows/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4), "higher_is_better": True,
@@ -419,18 +495,18 @@ def run_px(args):
             "config": {"workload": WORKLOAD, "fact_rows": NFACT, "dim_rows": NDIM, "nparts": NPARTS,
                        "attr_values": NATTR, "zipf_s": 1.1, "per_gpu_fact_rows": NFACT,
                        "l2": "inputs larger than L2 (1.22 GB of fact+dim columns per step vs 129 MB L2)",
-                       "parallelism": f"replicas x{world} (independent seeded shards)"},
+                       "parallelism": f"replicas x{world} (independent seeded shards)",
+                       "tuned_partition": {"fact": dict(zip(("items", "blocks_per_sm"), fcfg)),
+                                           "dim": dict(zip(("items", "blocks_per_sm"), dcfg))}},
             "operators": operators, "roofline": roofline, "fused_probe_partial": fused, "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": "rows/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "steps": e2e_steps, "runs_s": [round(x, 5) for x in runs],
                     "clock": "host wall clock around each synchronised run; median of three",
                     "overlap": "step k+1's host-to-device upload runs on a copy stream during step k's compute"},
             "gpu_launches": launches, "clocks": clk}
-    if rank == 0:
-        print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
-    return 0
+    return line if rank == 0 else None
 
 
 # ------------------------------------------------ batched fragments workload ----
@@ -527,9 +603,10 @@ def run_fragments(args):
                          "frac": round(alg / t_fused / 1e9 / peak, 4), "traffic": None,
                          "kernel": "frag_kernel (fused) + frag_emit_kernel, one px_fragments_run",
                          "alg_bytes_per_launch": alg, "peak_kind": f"{peak_kind} HBM copy bandwidth (burst)"},
-            "gpu_launches": fused_launches * args.steps, "clocks": clk}
-    print(json.dumps(line), flush=True)
-    return 0
+            "gpu_launches": fused_launches * args.steps, "clocks": clk,
+            "check": "fused batch == one-at-a-time calls on every fragment (keys and aggregates)"}
+    del batch, one, fs
+    return line
 
 
 # ------------------------------------------- plain and plain-join workloads ----
@@ -569,6 +646,30 @@ def _small_counts(which: str, p, res) -> dict:
         return {"rows": int(p.d["key"].numel()), "sel": int(res["nsel"].item())}
     return {"rows": int(p.d["fk"].numel()), "dim": int(p.d["pk"].numel()), "sel": int(res["nsel"].item()),
             "out": int(res["join"]["nout"].item())}
+
+
+def oracle_check_small(which: str, host: dict, res: dict) -> str:
+    """The small pipeline's result against the CPU oracle on the same input: the
+    selection count, the exchange offsets (plain) or the join count (plain join),
+    and every group (keys and aggregates, in key order)."""
+    import oracle
+    if which == "plain":
+        w = oracle.pipeline_plain(host, pxdata.CFG1_DATE_LO, pxdata.CFG1_DATE_HI, pxdata.CFG1_PARTS)
+        ok = int(res["nsel"].item()) == w["sel"].size and np.array_equal(res["offsets"].cpu().numpy(), w["offsets"])
+    else:
+        w = oracle.pipeline_join(host, pxdata.CFG2_DATE_LO, pxdata.CFG2_DATE_HI)
+        ok = int(res["nsel"].item()) == w["sel"].size and int(res["join"]["nout"].item()) == w["probe_rows"].size
+    g = res["groups"]
+    n = int(g["ngroups"].item())
+    keys = [t[:n].cpu().numpy().astype(np.int64) for t in g["keys"]]
+    order = np.lexsort(tuple(reversed(keys)))
+    ok = ok and n == w["groups"]["ngroups"]
+    ok = ok and all(np.array_equal(k[order], wk) for k, wk in zip(keys, w["groups"]["keys"]))
+    ok = ok and all(np.array_equal(a[:n].cpu().numpy()[order], wa) for a, wa in zip(g["aggs"], w["groups"]["aggs"]))
+    if not ok:
+        raise RuntimeError(f"{which}: GPU pipeline differs from the CPU oracle")
+    return "equal to the CPU oracle (selection count, " + ("exchange offsets" if which == "plain" else "join count") + \
+           ", every group's keys and aggregates)"
 
 
 def _same_groups(a: dict, b: dict) -> bool:
@@ -685,7 +786,7 @@ def run_small(args):
             oracle.pipeline_join(host, pxdata.CFG2_DATE_LO, pxdata.CFG2_DATE_HI)
         dt = time.perf_counter() - t0
         cpu = {"value": counts["rows"] / dt, "unit": "rows/s", "cores": 1, "kind": "oracle",
-               "sample": f"the whole {counts['rows']}-row input, one pipeline pass, {dt:.2f} s"}
+               "sample": f"the whole {counts['rows']}-row input, one pipeline pass, {dt:.2f} s", **host_cpu()}
     line = {"metric": "rows/s & % HBM peak per operator", "value": counts["rows"] / t_graph, "unit": "rows/s",
             "n_gpus": 1, "steps": nrep * copies, "warmup": args.warmup, "ms_per_step": round(1000 * t_graph, 4),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
@@ -703,8 +804,8 @@ def run_small(args):
             "gpu_launches": per_replay * nrep, "clocks": clk}
     if cpu:
         line["cpu_baseline"] = cpu
-    print(json.dumps(line), flush=True)
-    return 0
+    line["check"] = oracle_check_small(which, host, ref)
+    return line
 
 
 # ------------------------------------------------ late materialization ----
@@ -767,8 +868,7 @@ def run_late_mat(args):
                        "build_rows": int(d["pk_b"].size), "nparts": NPARTS},
             "late": out["late"], "eager": out["eager"],
             "speedup_late_vs_eager": out["eager"]["ms_per_step"] / out["late"]["ms_per_step"]}
-    print(json.dumps(line), flush=True)
-    return 0
+    return line
 
 
 # -------------------------------------------------------- serving workload ----
@@ -821,6 +921,18 @@ def make_trace(dims, pool, n, seed):
     return qs
 
 
+def same_query_result(a, b) -> bool:
+    """Equal (key, aggregates) group sets of two served queries (order-free)."""
+    na, nb = int(a.out[2].item()), int(b.out[2].item())
+    if na != nb:
+        return False
+    ka = a.out[0][:na].cpu().numpy().astype(np.int64)
+    kb = b.out[0][:nb].cpu().numpy().astype(np.int64)
+    oa, ob = np.argsort(ka, kind="stable"), np.argsort(kb, kind="stable")
+    return np.array_equal(ka[oa], kb[ob]) and all(
+        np.array_equal(x[:na].cpu().numpy()[oa], y[:nb].cpu().numpy()[ob]) for x, y in zip(a.out[1], b.out[1]))
+
+
 def run_serve(args):
     """Config 5: continuous batching against one-at-a-time service of the same
     Poisson arrivals, at 0.5x, 0.8x and 1.0x of the batched server's saturation QPS."""
@@ -843,12 +955,22 @@ def run_serve(args):
     sat = serving.Server(budget, max_batch=512).serve(fresh(2), np.zeros(n))
     one_sat = serving.OneAtATimeServer().serve(fresh(2)[: max(32, n // 8)], np.zeros(max(32, n // 8)))
     levels = []
+    mismatches = 0
     for f in (0.5, 0.8, 1.0):
         rate = f * sat["qps"]
         arr = serving.poisson_arrivals(rate, n, seed=int(100 * f))
-        b = serving.Server(budget, max_batch=512).serve(fresh(3), arr)
-        o = serving.OneAtATimeServer().serve(fresh(3), arr)
+        qb, qo = fresh(3), fresh(3)
+        b = serving.Server(budget, max_batch=512).serve(qb, arr)
+        o = serving.OneAtATimeServer().serve(qo, arr)
         levels.append({"offered_load": f, "offered_qps": rate, "batched": b, "one_at_a_time": o})
+        if f == 1.0:  # every query served in the mix equals the same query served alone
+            torch.cuda.synchronize()
+            mismatches = sum(0 if same_query_result(x, y) else 1 for x, y in zip(qb, qo))
+    if mismatches:
+        raise RuntimeError(f"served: {mismatches} queries differ between batched and one-at-a-time service")
+    nbig = sum(1 for q in qb if q.cols["key"].numel() >= 10_000_000)
+    check = (f"at 1.0x load all {n} queries ({nbig} at-scale) equal between continuous batching and "
+             "one-at-a-time service (keys and aggregates)")
     line = {"metric": "served QPS + p50/p99 latency vs one-at-a-time", "value": sat["qps"], "unit": "queries/s",
             "n_gpus": 1, "steps": n, "warmup": 64, "ms_per_step": round(1000 / sat["qps"], 4),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
@@ -856,9 +978,44 @@ def run_serve(args):
             "config": {"workload": SERVE_WORKLOAD if args.frag_scale == 1 else
                        f"REDUCED x{args.frag_scale:g}: " + SERVE_WORKLOAD,
                        "queries_per_level": n, "pool": len(pool), "resident_dims": len(dims)},
-            "saturation": {"batched": sat, "one_at_a_time": one_sat}, "levels": levels}
-    print(json.dumps(line), flush=True)
-    return 0
+            "saturation": {"batched": sat, "one_at_a_time": one_sat}, "levels": levels,
+            "check": check}
+    return line
+
+
+def emit(line) -> None:
+    if line is not None:
+        print(json.dumps(line), flush=True)
+
+
+def run_extras(args) -> dict:
+    """The other workloads of the headline metric, measured in the default run and
+    nested in its line: the 1M-row plain and 6M-row plain-join pipelines (cold
+    protocol per call, CUDA-graph stream per step, checked against the oracle),
+    the 512-fragment fused batch against one-at-a-time launches (checked equal),
+    and the served mix against one-at-a-time service (checked equal per query).
+    A sub-workload that fails reports its error here instead of hiding the rest."""
+    import copy
+    import gc
+    import torch
+    out = {}
+    for key, wl in (("plain", "plain"), ("plain_join", "plain-join"), ("fragments", "fragments"), ("served", "serve")):
+        a = copy.copy(args)
+        a.workload = wl
+        if wl == "fragments":
+            a.steps = min(args.steps, 50)
+        t0 = time.perf_counter()
+        try:
+            r = {"plain": run_small, "plain-join": run_small, "fragments": run_fragments, "serve": run_serve}[wl](a)
+            for k in ("n_gpus", "scaling", "vs_baseline", "dtype", "data"):
+                r.pop(k, None)
+        except Exception as e:  # noqa: BLE001 - reported in the line
+            r = {"error": f"{type(e).__name__}: {e}"}
+        r["wall_s"] = round(time.perf_counter() - t0, 1)
+        out[key] = r
+        gc.collect()
+        torch.cuda.empty_cache()
+    return out
 
 
 def main(argv=None):
@@ -870,6 +1027,8 @@ def main(argv=None):
     ap.add_argument("--cpu-sample", type=int, default=30_000_000,
                     help="fact rows of the oracle's CPU-baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--headline-only", action="store_true",
+                    help="only the at-scale pipeline (skip the plain, plain-join, fragments and served sub-records)")
     ap.add_argument("--fact-rows", type=int, default=None,
                     help="smaller fact side for profiling captures (the reported workload is then reduced)")
     ap.add_argument("--dim-rows", type=int, default=None)
@@ -890,33 +1049,26 @@ def main(argv=None):
         NFACT = args.fact_rows or NFACT
         NDIM = args.dim_rows or NDIM
         WORKLOAD = f"REDUCED for profiling: {NFACT}-row fact x {NDIM}-row dim; otherwise " + WORKLOAD
-    if args.workload in SMALL_WORKLOADS:
+    others = {"plain": (run_small, "the plain and plain-join lines carry the oracle as cpu_baseline"),
+              "plain-join": (run_small, "the plain and plain-join lines carry the oracle as cpu_baseline"),
+              "late-mat": (run_late_mat, "the late-materialization plan is compared with the eager plan"),
+              "serve": (run_serve, "the serving workload is compared with one-at-a-time GPU service"),
+              "fragments": (run_fragments, "the fragments workload is compared with one-at-a-time GPU calls")}
+    if args.workload in others:
+        fn, why = others[args.workload]
         if args.impl == "reference":
-            print(json.dumps({"impl": "reference", "unavailable": "the oracle reference arm covers the at-scale "
-                              "workload; the plain and plain-join lines carry the oracle as cpu_baseline"}))
+            emit({"impl": "reference", "unavailable": "the oracle reference arm covers the at-scale workload; " + why})
             return 0
-        return run_small(args)
-    if args.workload == "late-mat":
-        if args.impl == "reference":
-            print(json.dumps({"impl": "reference", "unavailable": "the oracle reference arm covers the at-scale "
-                              "workload; the late-materialization plan is compared with the eager plan"}))
-            return 0
-        return run_late_mat(args)
-    if args.workload == "serve":
-        if args.impl == "reference":
-            print(json.dumps({"impl": "reference", "unavailable": "the oracle reference arm covers the at-scale "
-                              "workload; the serving workload is compared with one-at-a-time GPU service"}))
-            return 0
-        return run_serve(args)
-    if args.workload == "fragments":
-        if args.impl == "reference":
-            print(json.dumps({"impl": "reference", "unavailable": "the oracle reference arm covers the at-scale "
-                              "workload; the fragments workload is compared with one-at-a-time GPU calls"}))
-            return 0
-        return run_fragments(args)
+        emit(fn(args))
+        return 0
     if args.impl == "reference":
-        return run_reference(args)
-    return run_px(args)
+        emit(run_reference(args))
+        return 0
+    line = run_px(args)
+    if line is not None and line["n_gpus"] == 1 and not args.headline_only and args.fact_rows is None:
+        line.update(run_extras(args))
+    emit(line)
+    return 0
 
 
 if __name__ == "__main__":

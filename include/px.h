@@ -156,12 +156,14 @@ px_status px_filter(const px_col* col, int64_t nrows, const int64_t* d_nrows,
  * of 262,400 bytes inside this library (held by every GPU that loads it until the
  * process exits), so nrows may not exceed PX_FILTER_NOALLOC_MAX_ROWS
  * (PX_ERR_UNSUPPORTED otherwise; use px_filter). It allocates nothing. d_status
- * (nullable, device int32) receives the call's device status word (PX_OK: the
- * filter sets no data-dependent error). The first call on each device looks up the array's device
- * address on that device (cudaGetSymbolAddress) and caches it; make that first
- * call before any stream capture. Every call on a device shares the one array and
- * clears what it uses at its start, so calls whose GPU work may overlap (other
- * streams, other threads) race and must be serialised by the caller. */
+ * (nullable, device int32) receives the call's device status, which is always
+ * PX_OK (the filter records no data-dependent error); it is kept so callers handle
+ * every entry point alike. The first call on each device looks up the array's
+ * device address on that device (cudaGetSymbolAddress) and caches it; make that
+ * first call before any stream capture. Every call on a device shares the one
+ * array (it keeps the last call's contents; each call writes every count it reads
+ * before reading it), so calls whose GPU work may overlap (other streams, other
+ * threads) race and must be serialised by the caller. */
 #define PX_FILTER_NOALLOC_MAX_ROWS 134217728LL /* 65536 tiles of 2048 rows */
 px_status px_filter_noalloc(const px_col* col, int64_t nrows, const int64_t* d_nrows,
                             int64_t lo, int64_t hi, int32_t* d_sel, int64_t* d_nsel,
@@ -186,6 +188,23 @@ px_status px_partition(const px_batch* in, int32_t key_col,
                        const int32_t* d_sel, const int64_t* d_nsel,
                        int32_t nparts, uint64_t seed, const px_batch* out,
                        int64_t* d_offsets, void* d_ws, size_t ws_bytes, void* stream);
+
+/* Launch shape of px_partition: rows per thread in a tile of 256 threads (2, 4 or
+ * 8, capped at the widest whose tile of every column fits the 48 KB staging
+ * area; 0 = that widest) and the most resident scatter blocks per SM (0 = as many
+ * as fit). Every shape gives the same result; they differ only in speed (an
+ * autotuner picks one per GPU and workload). */
+typedef struct {
+    int32_t items;
+    int32_t blocks_per_sm;
+} px_partition_config;
+
+/* px_partition with an explicit launch shape (cfg NULL = the defaults). */
+px_status px_partition_tuned(const px_batch* in, int32_t key_col,
+                             const int32_t* d_sel, const int64_t* d_nsel,
+                             int32_t nparts, uint64_t seed, const px_batch* out,
+                             int64_t* d_offsets, const px_partition_config* cfg,
+                             void* d_ws, size_t ws_bytes, void* stream);
 
 /* ---- hash join build (join build pipeline, Sec. 3.1) -------------------- */
 

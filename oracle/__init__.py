@@ -260,4 +260,5 @@ def pipeline_at_scale(d: dict, nparts: int, seed: int = 0) -> dict:
     final = groupby([partial["keys"][0]],
                     [(SUM, partial["aggs"][0], None), (SUM, partial["aggs"][1], None)])
     return {"dim_offsets": doff, "fact_offsets": foff, "join_offsets": jseg,
+            "dim_parts": dparts, "fact_parts": fparts, "probe_rows": pr, "build_rows": br,
             "partial": partial, "final": final}

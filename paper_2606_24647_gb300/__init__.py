@@ -31,7 +31,7 @@ PX_AGG_ACCUMULATE, PX_AGG_STREAM = 1, 2
 EXPORTED = [
     "px_ws_init", "px_stream_status", "px_last_error", "px_kernel_launches", "px_selftest_wait",
     "px_filter_ws_bytes", "px_filter", "px_filter_noalloc",
-    "px_partition_ws_bytes", "px_partition",
+    "px_partition_ws_bytes", "px_partition", "px_partition_tuned",
     "px_join_table_bytes", "px_join_build_ws_bytes", "px_join_build",
     "px_join_probe_ws_bytes", "px_join_probe",
     "px_groupby_ws_bytes", "px_groupby_agg", "px_groupby_agg_stream", "px_gather",
@@ -75,6 +75,10 @@ class px_fragment(ctypes.Structure):
                 ("d_out_aggs", ctypes.c_void_p * 4), ("d_ngroups", ctypes.c_void_p)]
 
 
+class px_partition_config(ctypes.Structure):
+    _fields_ = [("items", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32)]
+
+
 class px_fragments_config(ctypes.Structure):
     _fields_ = [("threads", ctypes.c_int32), ("items", ctypes.c_int32), ("chunk_rows", ctypes.c_int64),
                 ("blocks_per_sm", ctypes.c_int32)]
@@ -99,6 +103,7 @@ def _declare(lib):
         "px_filter_noalloc": ([CP, I64, P, I64, I64, P, P, P, P], I32),
         "px_partition_ws_bytes": ([I64, I32], SZ),
         "px_partition": ([BP, I32, P, P, I32, U64, BP, P, P, SZ, P], I32),
+        "px_partition_tuned": ([BP, I32, P, P, I32, U64, BP, P, ctypes.POINTER(px_partition_config), P, SZ, P], I32),
         "px_join_table_bytes": ([I64, I32], SZ),
         "px_join_build_ws_bytes": ([I64], SZ),
         "px_join_build": ([BP, I32, P, I32, I32, P, SZ, P, SZ, P], I32),
@@ -264,8 +269,9 @@ def px_filter(col, lo: int, hi: int, *, d_nrows=None, sel=None, nsel=None, ws=No
 
 
 def px_partition(cols, key_col: int, nparts: int, seed: int = 0, *, sel=None, nsel=None, d_nrows=None,
-                 out=None, offsets=None, ws=None, stream=None):
+                 out=None, offsets=None, config=None, ws=None, stream=None):
     """Hash repartition into nparts stable segments (the exchange, Sec. 3.1/3.3.2).
+    config: optional (items, blocks_per_sm) launch shape (px_partition_tuned).
 
     Returns (out_cols, offsets int64[nparts+1])."""
     L = load()
@@ -275,8 +281,14 @@ def px_partition(cols, key_col: int, nparts: int, seed: int = 0, *, sel=None, ns
     outb = _Batch(out, max(n, 1))
     offsets = offsets if offsets is not None else torch.empty(nparts + 1, dtype=torch.int64, device=cols[0].device)
     ws = _ws(ws, L.px_partition_ws_bytes(n, nparts), stream)
-    _check(L.px_partition(inb.ref(), key_col, _sel_ptr(sel), _ptr(nsel), nparts, int(seed) & (2**64 - 1), outb.ref(),
-                          _ptr(offsets), ws.ptr, ws.nbytes, _stream(stream)), "px_partition")
+    if config is None:
+        _check(L.px_partition(inb.ref(), key_col, _sel_ptr(sel), _ptr(nsel), nparts, int(seed) & (2**64 - 1),
+                              outb.ref(), _ptr(offsets), ws.ptr, ws.nbytes, _stream(stream)), "px_partition")
+    else:
+        cfg = px_partition_config(*config)
+        _check(L.px_partition_tuned(inb.ref(), key_col, _sel_ptr(sel), _ptr(nsel), nparts, int(seed) & (2**64 - 1),
+                                    outb.ref(), _ptr(offsets), ctypes.byref(cfg), ws.ptr, ws.nbytes,
+                                    _stream(stream)), "px_partition")
     return out, offsets
 
 

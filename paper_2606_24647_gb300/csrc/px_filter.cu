@@ -197,9 +197,9 @@ px_status px_filter(const px_col* col, int64_t nrows, const int64_t* d_nrows, in
 // memory, so cannot provide a workspace: e.g. code running under a host engine
 // whose memory manager owns every device byte and forbids side allocations, or a
 // serving loop that reserves all memory at start-up and must not call cudaMalloc
-// (which can synchronise the device) on its hot path. Its scratch (the status
-// word, the tile counter and one look-back state per tile) lives in the
-// file-scope device array below instead of a caller workspace.
+// (which can synchronise the device) on its hot path. Its scratch (one count per
+// tile, after a header kept for the workspace layout the filter kernels share)
+// lives in the file-scope device array below instead of a caller workspace.
 namespace px {
 namespace {
 
@@ -256,15 +256,15 @@ extern "C" px_status px_filter_noalloc(const px_col* col, int64_t nrows, const i
     const int64_t ntiles = cdiv(nrows, kTile);
     if (kWsScratch + static_cast<size_t>(ntiles) * 4 > kNoallocScratchBytes)
         return fail(PX_ERR_UNSUPPORTED, "px_filter_noalloc: %lld tiles exceed the static scratch", (long long)ntiles);
-    // Each call clears the status word (the array keeps whatever the previous call
-    // left there); every count it uses is written before it is read.
-    cudaMemsetAsync(scratch, 0, kWsScratch, st);
+    // The array keeps whatever the previous call left there; every count a call
+    // uses is written before it is read, so nothing needs clearing. The filter
+    // records no data-dependent error, so the status is always PX_OK.
     if (nrows == 0) {
         cudaMemsetAsync(d_nsel, 0, sizeof(int64_t), st);
     } else {
         int32_t* cnt = reinterpret_cast<int32_t*>(static_cast<char*>(scratch) + kWsScratch);
         launch_filter_type(col->type, col->data, nrows, d_nrows, lo, hi, d_sel, d_nsel, cnt, ntiles, st);
     }
-    if (d_status) cudaMemcpyAsync(d_status, scratch, sizeof(int32_t), cudaMemcpyDeviceToDevice, st);
+    if (d_status) cudaMemsetAsync(d_status, 0, sizeof(int32_t), st);
     return check_launch("px_filter_noalloc");
 }

@@ -20,6 +20,7 @@
 //                partition's run contiguously, so the stores coalesce.
 // The key column is read twice (hist and scatter); every other column once; every
 // column written once.
+#include <algorithm>
 #include <type_traits>
 
 #include "px_common.cuh"
@@ -211,7 +212,7 @@ __device__ __forceinline__ void stage_plain(const T* in, T* staged, const int32_
 // NBITS: bits of the largest partition id (nparts - 1), so the multi-split below
 // is unrolled: one ballot per id bit, plus one for the valid rows of a ragged tile.
 template <int ITEMS, int NBITS>
-__global__ void __launch_bounds__(kThreads, 3)
+__global__ void __launch_bounds__(kThreads, ITEMS >= 8 ? 3 : 4)
 part_scatter_kernel(Cols cols, int32_t key_col, const int32_t* __restrict__ sel,
                     const int64_t* __restrict__ d_nsel, int64_t ncap, uint64_t seed, uint32_t nparts,
                     const int32_t* __restrict__ offs, int64_t ntiles, uint32_t stage_bytes, uint32_t row_bytes,
@@ -420,10 +421,14 @@ PartScratch part_scratch(void* d_ws, int64_t nrows, int64_t ntiles, int32_t npar
     return p;
 }
 
+// blocks_per_sm > 0 caps the scatter's resident blocks per SM by asking each
+// block for a larger share of the SM's shared memory than it needs (a launch
+// shape the autotuner explores); 0 leaves residency to the kernel's own needs.
 template <int ITEMS>
 px_status launch_partition(const Cols& cols, int32_t key_col, const int32_t* d_sel, const int64_t* d_n, int64_t ncap,
                            uint64_t seed, int32_t nparts, int64_t* d_offsets, const PartScratch& ps, int64_t ntiles,
-                           uint32_t stage_bytes, uint32_t row_bytes, int32_t* status, cudaStream_t st) {
+                           uint32_t stage_bytes, uint32_t row_bytes, int32_t blocks_per_sm, int32_t* status,
+                           cudaStream_t st) {
     px_status s;
     const int64_t* key = static_cast<const int64_t*>(cols.in[key_col]);
     part_hist_kernel<ITEMS><<<static_cast<unsigned>(ntiles), kThreads, kWarps * nparts * sizeof(int32_t), st>>>(
@@ -440,7 +445,18 @@ px_status launch_partition(const Cols& cols, int32_t key_col, const int32_t* d_s
     note_launch();
     if ((s = check_launch("px_partition scan")) != PX_OK) return s;
 
-    const size_t smem = scatter_smem_bytes(ITEMS, stage_bytes, nparts);
+    size_t smem = scatter_smem_bytes(ITEMS, stage_bytes, nparts);
+    if (blocks_per_sm > 0) {
+        int dev = 0, per_sm_smem = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&per_sm_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+        // each resident block also holds 1 KB the system reserves
+        const size_t share = static_cast<size_t>(per_sm_smem) / blocks_per_sm;
+        const size_t want = share > 1024 + 16 ? share - 1024 - 16 : 0;
+        int max_block = 0;
+        cudaDeviceGetAttribute(&max_block, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        if (want > smem) smem = std::min(want, static_cast<size_t>(max_block));
+    }
     auto go = [&](auto kern) {
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
         kern<<<static_cast<unsigned>(ntiles), kThreads, smem, st>>>(cols, key_col, d_sel, d_n, ncap, seed,
@@ -479,9 +495,9 @@ size_t px_partition_ws_bytes(int64_t nrows, int32_t nparts) {
     return kWsScratch + 2 * part_mat_bytes(nrows, nparts) + scan_scratch_bytes(cdiv(max_tiles * nparts, kScanTile));
 }
 
-px_status px_partition(const px_batch* in, int32_t key_col, const int32_t* d_sel, const int64_t* d_nsel,
-                       int32_t nparts, uint64_t seed, const px_batch* out, int64_t* d_offsets, void* d_ws,
-                       size_t ws_bytes, void* stream) {
+px_status px_partition_tuned(const px_batch* in, int32_t key_col, const int32_t* d_sel, const int64_t* d_nsel,
+                             int32_t nparts, uint64_t seed, const px_batch* out, int64_t* d_offsets,
+                             const px_partition_config* cfg, void* d_ws, size_t ws_bytes, void* stream) {
     CallRange nvtx_range("px_partition");
     set_error("");
     px_status s = check_batch(in, "px_partition in");
@@ -504,6 +520,15 @@ px_status px_partition(const px_batch* in, int32_t key_col, const int32_t* d_sel
         return fail(PX_ERR_INVALID, "px_partition: out capacity %lld below input rows %lld",
                     (long long)out->nrows, (long long)in->nrows);
     if (!d_offsets) return fail(PX_ERR_INVALID, "px_partition: null d_offsets");
+    int32_t items_req = 0, bps = 0;
+    if (cfg) {
+        if (cfg->items != 0 && cfg->items != 2 && cfg->items != 4 && cfg->items != 8)
+            return fail(PX_ERR_INVALID, "px_partition: config items %d (0, 2, 4 or 8)", cfg->items);
+        if (cfg->blocks_per_sm < 0 || cfg->blocks_per_sm > 32)
+            return fail(PX_ERR_INVALID, "px_partition: config blocks_per_sm %d (0..32)", cfg->blocks_per_sm);
+        items_req = cfg->items;
+        bps = cfg->blocks_per_sm;
+    }
     const int64_t ncap = in->nrows;
     s = check_ws(d_ws, ws_bytes, px_partition_ws_bytes(ncap, nparts), "px_partition");
     if (s != PX_OK) return s;
@@ -527,7 +552,10 @@ px_status px_partition(const px_batch* in, int32_t key_col, const int32_t* d_sel
     for (int w : {8, 4, 1})
         for (int c = 0; c < in->ncols; ++c)
             if (cols.width[c] == w) cols.order[n_ord++] = c;
-    const int items = items_for(row_bytes);
+    // Rows per thread: the caller's choice when a tile of every column fits the
+    // staging budget, else the widest that fits.
+    const int fit = items_for(row_bytes);
+    const int items = items_req > 0 && items_req <= fit ? items_req : fit;
     const int64_t T = static_cast<int64_t>(kThreads) * items;
     uint32_t stage_bytes = 0;
     for (int c = 0; c < in->ncols; ++c) {
@@ -540,12 +568,19 @@ px_status px_partition(const px_batch* in, int32_t key_col, const int32_t* d_sel
     const int64_t* d_n = d_sel ? d_nsel : in->d_nrows;
     if (items == 8)
         return launch_partition<8>(cols, key_col, d_sel, d_n, ncap, seed, nparts, d_offsets, ps, ntiles, stage_bytes,
-                                   row_bytes, status, st);
+                                   row_bytes, bps, status, st);
     if (items == 4)
         return launch_partition<4>(cols, key_col, d_sel, d_n, ncap, seed, nparts, d_offsets, ps, ntiles, stage_bytes,
-                                   row_bytes, status, st);
+                                   row_bytes, bps, status, st);
     return launch_partition<2>(cols, key_col, d_sel, d_n, ncap, seed, nparts, d_offsets, ps, ntiles, stage_bytes,
-                               row_bytes, status, st);
+                               row_bytes, bps, status, st);
+}
+
+px_status px_partition(const px_batch* in, int32_t key_col, const int32_t* d_sel, const int64_t* d_nsel,
+                       int32_t nparts, uint64_t seed, const px_batch* out, int64_t* d_offsets, void* d_ws,
+                       size_t ws_bytes, void* stream) {
+    return px_partition_tuned(in, key_col, d_sel, d_nsel, nparts, seed, out, d_offsets, nullptr, d_ws, ws_bytes,
+                              stream);
 }
 
 }  // extern "C"

@@ -146,10 +146,13 @@ class AtScalePipeline:
                    "px_groupby_agg(final)"]
 
     def __init__(self, d: dict, nparts: int = 64, seed: int = 0, nattr_bound: int = 10_000, attr_range="auto",
-                 fused: bool = False):
+                 fused: bool = False, fact_config=None, dim_config=None):
         L = load()
         self.d = d
         self.fused = fused  # probe + Partial group-by in one call (px_join_probe_agg)
+        # launch shapes (items, blocks per SM) of the two exchanges, e.g. from
+        # autotune.tune_partition; None = the library's defaults
+        self.fact_config, self.dim_config = fact_config, dim_config
         self.nparts, self.seed = nparts, seed
         # catalog statistic of dim.attr (speed only); "auto": the attribute's domain [0, nattr_bound)
         self.attr_range = (0, nattr_bound - 1) if attr_range == "auto" else attr_range
@@ -184,9 +187,11 @@ class AtScalePipeline:
         rng = [self.attr_range] if self.attr_range else None
         mark = mark or (lambda i: None)
         mark(0)
-        px_partition(self.dim, 0, P, self.seed, out=self.dparts, offsets=self.doff, ws=ws, stream=stream)
+        px_partition(self.dim, 0, P, self.seed, out=self.dparts, offsets=self.doff, config=self.dim_config, ws=ws,
+                     stream=stream)
         mark(1)
-        px_partition(self.fact, 0, P, self.seed, out=self.fparts, offsets=self.foff, ws=ws, stream=stream)
+        px_partition(self.fact, 0, P, self.seed, out=self.fparts, offsets=self.foff, config=self.fact_config, ws=ws,
+                     stream=stream)
         mark(2)
         px_join_build(self.dparts, 0, seg=self.doff, unique=True, table=self.table, ws=ws, stream=stream)
         mark(3)
@@ -209,9 +214,11 @@ class AtScalePipeline:
         lo, hi = self.attr_range
         mark = mark or (lambda i: None)
         mark(0)
-        px_partition(self.dim, 0, P, self.seed, out=self.dparts, offsets=self.doff, ws=ws, stream=stream)
+        px_partition(self.dim, 0, P, self.seed, out=self.dparts, offsets=self.doff, config=self.dim_config, ws=ws,
+                     stream=stream)
         mark(1)
-        px_partition(self.fact, 0, P, self.seed, out=self.fparts, offsets=self.foff, ws=ws, stream=stream)
+        px_partition(self.fact, 0, P, self.seed, out=self.fparts, offsets=self.foff, config=self.fact_config, ws=ws,
+                     stream=stream)
         mark(2)
         px_join_build(self.dparts, 0, seg=self.doff, unique=True, table=self.table, ws=ws, stream=stream)
         mark(3)

@@ -52,3 +52,20 @@ def test_unreadable_cache_is_empty(tmp_path):
     p = tmp_path / "bad.json"
     p.write_text("{not json")
     assert autotune.load_cache(str(p)) == {}
+
+
+def test_partition_grid_points_are_valid_configurations():
+    assert len(set(autotune.PARTITION_GRID)) == len(autotune.PARTITION_GRID)
+    for items, bps in autotune.PARTITION_GRID:
+        assert items in (2, 4, 8) and 0 <= bps <= 32
+
+
+def test_partition_and_fragment_entries_share_one_cache_without_clashing(tmp_path):
+    path = str(tmp_path / "tune.json")
+    key = autotune.gpu_key("NVIDIA GB300", 10, 3, 152)
+    a = autotune.cached_or_search(key, "partition|fact", lambda p: 1.0 if p != (4, 3) else 0.1,
+                                  grid=autotune.PARTITION_GRID, path=path)
+    b = autotune.cached_or_search(key, "fragments512x1", lambda p: 1.0 if p != autotune.GRID[2] else 0.1, path=path)
+    assert a == (4, 3) and b == autotune.GRID[2]
+    entries = autotune.load_cache(path)
+    assert entries[f"{key}|partition|fact"] == [4, 3] and entries[f"{key}|fragments512x1"] == list(autotune.GRID[2])

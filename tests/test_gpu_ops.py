@@ -394,3 +394,18 @@ def test_bounded_wait_times_out_and_context_stays_usable(px):
     assert count(nsel) == 10
     with pytest.raises(px.PxError):
         px.px_selftest_wait(flag, 0, status)
+
+
+def test_partition_every_launch_shape_gives_the_same_result(px):
+    """Every point of the autotuner's exchange grid: identical offsets and columns
+    (equal to the oracle's), on a skewed input spanning many tiles per block."""
+    from paper_2606_24647_gb300 import autotune
+    d = pxdata.plain_at_scale(20_000, 700_001, nattr=100, seed=31)
+    cols_np = [d["fk"], d["amount"], d["date"]]
+    cols = [dev(c) for c in cols_np]
+    want, woff = oracle.partition(cols_np, 0, 64, 0)
+    for cfg in autotune.PARTITION_GRID + [(0, 0)]:
+        out, off = px.px_partition(cols, 0, 64, 0, config=cfg)
+        np.testing.assert_array_equal(host(off), woff)
+        for c in range(3):
+            np.testing.assert_array_equal(host(out[c]), want[c])

@@ -1,11 +1,8 @@
 """GPU parity of the three workload pipelines against the oracle.
 
-Reduced sizes are compared element by element with the oracle's pipelines. At the
-full workload sizes (1M-row plain batch; 200k x 6M plain join; 2M x 60M skewed
-join at 64 partitions, the launch configuration the bench times) the small ones
-are compared in full, and the large ones on sampled rows the oracle computes one
-by one plus closed forms of the generators (every fact key names exactly one
-dimension row, so each group's SUM/COUNT is a lookup-and-add over the fact rows).
+Reduced sizes and the full workload sizes (1M-row plain batch; 200k x 6M plain
+join; 2M x 60M skewed join at 64 partitions, the launch configuration the bench
+times) are all compared element by element with the oracle's pipelines.
 """
 import numpy as np
 import pytest
@@ -81,52 +78,30 @@ def test_at_scale_pipeline_small(px):
 
 
 def test_at_scale_pipeline_full_size(px):
-    """60M-row Zipf fact x 2M dim, 64 partitions: the configuration the bench times."""
+    """60M-row Zipf fact x 2M dim, 64 partitions: the configuration the bench times,
+    compared element by element with the oracle's pipeline on the same input: both
+    exchanges (offsets and every column of every partition, in order), the join
+    (output segment offsets and every joined row), the Partial groups with their
+    segments and the Final groups."""
     d = pxdata.plain_at_scale()
     nf, nd = d["fk"].size, d["pk"].size
     p = AtScalePipeline(_to_dev(d), nparts=64)
     r = p.run()
     assert p.ws.status() == px.PX_OK
-    # Exchange: the partition of every distinct key comes from the oracle one by one;
-    # offsets must equal the per-partition row counts, and whole segments (the
-    # hottest partition and two others) must hold exactly the input rows of that
-    # partition in input order (stability).
-    uniq, inv, cnt = np.unique(d["fk"], return_inverse=True, return_counts=True)
-    part_u = oracle.part_of_array(uniq, 0, 64)
-    want_foff = np.concatenate([[0], np.cumsum(np.bincount(part_u, weights=cnt, minlength=64).astype(np.int64))])
-    np.testing.assert_array_equal(host(r["fact_offsets"]), want_foff)
-    part_pk = oracle.part_of_array(d["pk"], 0, 64)
-    want_doff = np.concatenate([[0], np.cumsum(np.bincount(part_pk, minlength=64))])
-    np.testing.assert_array_equal(host(r["dim_offsets"]), want_doff)
-    part_row = part_u[inv]
-    hot = int(np.argmax(np.diff(want_foff)))
-    for q in sorted({hot, 0, 63}):
-        mask = part_row == q
-        a, b = int(want_foff[q]), int(want_foff[q + 1])
-        for c, name in enumerate(["fk", "amount", "date"]):
-            np.testing.assert_array_equal(host(p.fparts[c][a:b]), d[name][mask])
-        m = part_pk == q
-        for c, name in enumerate(["pk", "attr"]):
-            np.testing.assert_array_equal(host(p.dparts[c][int(want_doff[q]):int(want_doff[q + 1])]), d[name][m])
-    # Join: every fact row matches once (pk is a permutation), so nout = nf.
-    assert count(r["join"]["nout"]) == nf
-    # Final groups: closed form via the permutation (attr of fk = attr[pos_of_pk[fk]]).
-    pos = np.empty(nd + 1, np.int64)
-    pos[d["pk"]] = np.arange(nd)
-    attr_of = d["attr"][pos[d["fk"]]]
-    sums = np.bincount(attr_of, weights=d["amount"].astype(np.float64), minlength=10_000)
-    cnts = np.bincount(attr_of, minlength=10_000)
-    fin = r["final"]
-    ng = count(fin["ngroups"])
-    keys = host(fin["keys"][0], ng)
-    order = np.argsort(keys)
-    keys = keys[order]
-    np.testing.assert_array_equal(keys, np.nonzero(cnts)[0])
-    np.testing.assert_array_equal(host(fin["aggs"][1], ng)[order], cnts[keys])
-    np.testing.assert_array_equal(host(fin["aggs"][0], ng)[order], sums[keys].astype(np.int64))
-    # Partial groups sum to the final ones and count every joined row.
-    pc = host(r["partial"]["aggs"][1], count(r["partial"]["ngroups"]))
-    assert int(pc.sum()) == nf
+    w = oracle.pipeline_at_scale(d, 64)
+    np.testing.assert_array_equal(host(r["dim_offsets"]), w["dim_offsets"])
+    np.testing.assert_array_equal(host(r["fact_offsets"]), w["fact_offsets"])
+    for c in range(3):
+        np.testing.assert_array_equal(host(p.fparts[c], nf), w["fact_parts"][c])
+    for c in range(2):
+        np.testing.assert_array_equal(host(p.dparts[c], nd), w["dim_parts"][c])
+    m = count(r["join"]["nout"])
+    assert m == w["probe_rows"].size == nf  # every fact key names one dimension row
+    np.testing.assert_array_equal(host(r["join"]["out_seg"]), w["join_offsets"])
+    np.testing.assert_array_equal(host(p.jout[0], m), w["fact_parts"][1][w["probe_rows"]])
+    np.testing.assert_array_equal(host(p.jout[1], m), w["dim_parts"][1][w["build_rows"]])
+    assert_groups_equal(r["partial"], w["partial"], 1, segmented=True)
+    assert_groups_equal(r["final"], w["final"], 1)
 
 
 @pytest.mark.parametrize("which", ["plain", "join"])
