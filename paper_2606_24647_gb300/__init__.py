@@ -384,6 +384,46 @@ def px_groupby_agg(cols, key_cols, aggs, *, max_groups: int, sel=None, nsel=None
     return res
 
 
+def fragment_descriptor(f: dict) -> tuple:
+    """The px_fragment descriptor of one fragment dict (see FragmentBatch), its
+    result tensors {'keys', 'aggs', 'ngroups'} (the dict's 'out' = (keys, [aggs],
+    ngroups) when given, else allocated here) and the tensors the descriptor points
+    to (kept alive with it)."""
+    d = px_fragment()
+    key = f["key"]
+    dev = key.device
+    d.nrows = key.numel()
+    d.key = _col(key)
+    if f.get("filter") is not None:
+        d.filter = _col(f["filter"])
+        d.lo, d.hi = int(f["lo"]), int(f["hi"])
+    cols = list(f.get("cols", []))
+    d.ncols = len(cols)
+    for c, t in enumerate(cols):
+        d.cols[c] = _col(t)
+    aggs = list(f.get("aggs", []))
+    d.naggs = len(aggs)
+    for a, (op, x, y) in enumerate(aggs):
+        d.aggs[a] = px_agg(op, -1 if x is None else x, -1 if y is None else y)
+    d.d_table = _ptr(f["table"])
+    d.nbuild = f["group"].numel()
+    d.group = _col(f["group"])
+    d.group_lo, d.group_hi = int(f["group_lo"]), int(f["group_hi"])
+    mg = int(f["max_groups"])
+    d.max_groups = mg
+    if f.get("out") is not None:  # caller-provided outputs: (keys, [aggs...], ngroups)
+        keys, outs, ng = f["out"][0], list(f["out"][1]), f["out"][2]
+    else:
+        keys = torch.empty(max(mg, 1), dtype=f["group"].dtype, device=dev)
+        outs = [torch.empty(max(mg, 1), dtype=torch.int64, device=dev) for _ in aggs]
+        ng = torch.zeros(1, dtype=torch.int64, device=dev)
+    d.d_out_keys = keys.data_ptr()
+    for a, t in enumerate(outs):
+        d.d_out_aggs[a] = t.data_ptr()
+    d.d_ngroups = ng.data_ptr()
+    return d, {"keys": keys, "aggs": outs, "ngroups": ng}, [key, f.get("filter"), f["table"], f["group"], *cols]
+
+
 class FragmentBatch:
     """A batch of fused filter -> join probe -> aggregate fragments (px_fragments_run).
 
@@ -396,48 +436,21 @@ class FragmentBatch:
     pinned plan staging buffer lives with the batch."""
 
     def __init__(self, frags: list, config: tuple | None = None, ws: Workspace | None = None,
-                 plan: torch.Tensor | None = None):
+                 plan: torch.Tensor | None = None, prepared: list | None = None):
+        """frags: fragment dicts; or prepared: (descriptor, results, tensors) triples
+        from fragment_descriptor, built once per fragment and reused across batches
+        (a serving loop forms a batch by copying descriptors only)."""
         L = load()
-        self.n = len(frags)
+        if prepared is None:
+            prepared = [fragment_descriptor(f) for f in frags]
+        self.n = len(prepared)
         self.frags = frags
-        dev = frags[0]["key"].device if frags else torch.device("cuda", torch.cuda.current_device())
         arr = (px_fragment * max(1, self.n))()
-        self.results = []
-        self._keep = []
-        for i, f in enumerate(frags):
-            d = arr[i]
-            key = f["key"]
-            d.nrows = key.numel()
-            d.key = _col(key)
-            if f.get("filter") is not None:
-                d.filter = _col(f["filter"])
-                d.lo, d.hi = int(f["lo"]), int(f["hi"])
-            cols = list(f.get("cols", []))
-            d.ncols = len(cols)
-            for c, t in enumerate(cols):
-                d.cols[c] = _col(t)
-            aggs = list(f.get("aggs", []))
-            d.naggs = len(aggs)
-            for a, (op, x, y) in enumerate(aggs):
-                d.aggs[a] = px_agg(op, -1 if x is None else x, -1 if y is None else y)
-            d.d_table = _ptr(f["table"])
-            d.nbuild = f["group"].numel()
-            d.group = _col(f["group"])
-            d.group_lo, d.group_hi = int(f["group_lo"]), int(f["group_hi"])
-            mg = int(f["max_groups"])
-            d.max_groups = mg
-            if "out" in f:  # caller-provided outputs: (keys, [aggs...], ngroups)
-                keys, outs, ng = f["out"][0], list(f["out"][1]), f["out"][2]
-            else:
-                keys = torch.empty(max(mg, 1), dtype=f["group"].dtype, device=dev)
-                outs = [torch.empty(max(mg, 1), dtype=torch.int64, device=dev) for _ in aggs]
-                ng = torch.zeros(1, dtype=torch.int64, device=dev)
-            d.d_out_keys = keys.data_ptr()
-            for a, t in enumerate(outs):
-                d.d_out_aggs[a] = t.data_ptr()
-            d.d_ngroups = ng.data_ptr()
-            self.results.append({"keys": keys, "aggs": outs, "ngroups": ng})
-            self._keep += [key, f.get("filter"), f["table"], f["group"], *cols]
+        for i, (d, _, _) in enumerate(prepared):
+            arr[i] = d
+        self.results = [r for _, r, _ in prepared]
+        self._keep = [k for _, _, k in prepared]
+        dev = self.results[0]["keys"].device if prepared else torch.device("cuda", torch.cuda.current_device())
         self.arr = arr
         self.cfg = None
         if config is not None:

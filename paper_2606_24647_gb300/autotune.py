@@ -15,7 +15,7 @@ from __future__ import annotations
 import json
 import os
 
-GRID = [(t, i, c, b) for t in (256, 512) for i in (2, 4) for c in (16384, 65536, 262144) for b in (1, 2, 4, 8)]
+GRID = [(t, i, c, b) for t in (256, 512) for i in (2, 4) for c in (0, 16384, 65536, 262144) for b in (1, 2, 4, 8)]
 # px_partition: (rows per thread, most resident blocks per SM; 0 = as many as fit);
 # rows per thread wider than the columns allow are narrowed by the library.
 PARTITION_GRID = [(4, 0), (4, 3), (4, 2), (8, 0), (8, 2)]

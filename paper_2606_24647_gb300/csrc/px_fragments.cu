@@ -447,11 +447,21 @@ px_status px_fragments_run(const px_fragment* frags, int32_t nfrags, const px_fr
         const px_status s = check_fragment(frags[i], i);
         if (s != PX_OK) return s;
     }
-    px_fragments_config c = {256, 2, 65536, 8};
+    px_fragments_config c = {256, 2, 0, 8};
     if (cfg) c = *cfg;
     if ((c.threads != 256 && c.threads != 512) || (c.items != 2 && c.items != 4) || c.blocks_per_sm < 1 ||
-        c.blocks_per_sm > 8 || c.chunk_rows < 1 || c.chunk_rows % (static_cast<int64_t>(c.threads) * c.items) != 0)
+        c.blocks_per_sm > 8 || c.chunk_rows < 0 || c.chunk_rows % (static_cast<int64_t>(c.threads) * c.items) != 0)
         return fail(PX_ERR_INVALID, "px_fragments_run: bad configuration");
+    if (c.chunk_rows == 0) {
+        // Rows per work item from the batch: about four items per block of the
+        // persistent grid, so a small batch still spreads over every SM, within
+        // [one tile, 65536 rows].
+        const int64_t tile = static_cast<int64_t>(c.threads) * c.items;
+        int64_t rows = 0;
+        for (int32_t i = 0; i < nfrags; ++i) rows += frags[i].nrows;
+        const int64_t want = cdiv(rows, 4 * static_cast<int64_t>(sm_count()) * c.blocks_per_sm);
+        c.chunk_rows = std::min<int64_t>(std::max<int64_t>(cdiv(want, tile) * tile, tile), cdiv(65536, tile) * tile);
+    }
     const PlanLayout PL = plan_layout(nfrags);
     if (!h_plan || plan_bytes < PL.total)
         return fail(PX_ERR_INVALID, "px_fragments_run: plan staging of %zu bytes, %zu needed", plan_bytes, PL.total);

@@ -83,17 +83,30 @@ class Query:
     """One fragment query: filter date in [lo, hi) on its probe batch, join key = the
     named dimension's pk, group by dimension attr: SUM(price), SUM(price*qty), COUNT."""
 
-    __slots__ = ("qid", "dim", "cols", "lo", "hi", "arrival", "admitted", "done", "out", "nbytes")
+    __slots__ = ("qid", "dim", "cols", "lo", "hi", "arrival", "admitted", "done", "out", "nbytes", "prepared")
 
     def __init__(self, qid: int, dim: ResidentDim, cols: dict, lo: int, hi: int):
         self.qid, self.dim, self.cols, self.lo, self.hi = qid, dim, cols, lo, hi
         self.arrival = self.admitted = self.done = None
         self.out = None
+        self.prepared = None
         n = int(cols["key"].numel())
         g = dim.ngroups
         # working memory charged while in flight: the probe batch, the dense
         # accumulators and flags, and the outputs
         self.nbytes = 28 * n + 25 * g + 28 * g
+
+    def prepare(self) -> None:
+        """Result buffers and the fused-batch descriptor, built once when the query
+        is created (as a request carries its result buffer), so that forming a batch
+        only copies descriptors."""
+        from . import fragment_descriptor
+        dev = self.cols["key"].device
+        g = self.dim.ngroups
+        self.out = (torch.empty(g, dtype=self.dim.attr.dtype, device=dev),
+                    [torch.empty(g, dtype=torch.int64, device=dev) for _ in range(3)],
+                    torch.zeros(1, dtype=torch.int64, device=dev))
+        self.prepared = fragment_descriptor(self.fragment())
 
     def fragment(self) -> dict:
         c, d = self.cols, self.dim
@@ -120,13 +133,6 @@ class Server:
                       for _ in range(inflight)]
         self.wss = [Workspace(1 << 24) for _ in range(inflight)]
         self.batches = 0
-
-    def _alloc_out(self, q: Query):
-        dev = q.cols["key"].device
-        g = q.dim.ngroups
-        q.out = (torch.empty(g, dtype=q.dim.attr.dtype, device=dev),
-                 [torch.empty(g, dtype=torch.int64, device=dev) for _ in range(3)],
-                 torch.zeros(1, dtype=torch.int64, device=dev))
 
     def serve(self, queries: list, arrivals, clock=time.perf_counter) -> dict:
         """Serve queries arriving at `arrivals` (seconds from the start, ascending).
@@ -158,12 +164,13 @@ class Server:
                     q = waiting.popleft()
                     self.adm.admit(q.nbytes)
                     q.admitted = clock() - t0
-                    self._alloc_out(q)
+                    if q.prepared is None:
+                        q.prepare()
                     batch.append(q)
                 if batch:
                     slot = free_slots.pop()
-                    fb = FragmentBatch([q.fragment() for q in batch], config=self.config, ws=self.wss[slot],
-                                       plan=self.plans[slot])
+                    fb = FragmentBatch(None, config=self.config, ws=self.wss[slot], plan=self.plans[slot],
+                                       prepared=[q.prepared for q in batch])
                     self.wss[slot] = fb.ws
                     fb.run(self.stream)
                     ev = torch.cuda.Event()
