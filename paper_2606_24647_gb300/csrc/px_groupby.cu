@@ -715,6 +715,146 @@ groupby_kernel(Spec sp, const int32_t* __restrict__ sel, const int64_t* __restri
     }
 }
 
+// Dense aggregation of the most common Partial shape (a join's output grouped by
+// the gathered dimension attribute): one key column KT, SUM of one column VT and
+// COUNT, no selection, a key range wide enough that one shared-memory replica of
+// its slots serves every warp of the block without much collision, and a dense
+// global result. Same contract as the dense block mode of groupby_kernel with
+// far fewer instructions per row: each thread takes ITEMS consecutive rows with
+// 16-byte vector loads, the SUM is held as 32-bit words (an atomic add on the low
+// word returns the carry into the high word), COUNT is a plain 32-bit reduction,
+// hot keys (lane 0's slot shared by >= kMajority lanes) are summed across the warp
+// first, and each segment's slots are flushed into the dense global array.
+// Rows whose key lies outside the range take the global hash path.
+template <typename KT, typename VT, int ITEMS>
+__global__ void __launch_bounds__(kThreads, 1)
+groupby_sum_count_kernel(Spec sp, int32_t sum_slot, int32_t cnt_slot, const int64_t* __restrict__ d_n, int64_t ncap,
+                         const int64_t* __restrict__ d_seg, GTable g, int64_t max_groups, int32_t* __restrict__ out_seg,
+                         int32_t* status) {
+    constexpr int T = kThreads * ITEMS;
+    static_assert(ITEMS * sizeof(KT) % 16 == 0 && ITEMS * sizeof(VT) % 16 == 0, "whole 16-byte loads per thread");
+    extern __shared__ __align__(16) uint32_t s_acc[];  // low words [D], high words [D], counts [D]
+    const uint32_t D = sp.D;
+    uint32_t* s_lo = s_acc;
+    uint32_t* s_hi = s_acc + D;
+    uint32_t* s_cnt = s_acc + 2 * static_cast<size_t>(D);
+    const int tid = threadIdx.x, lane = tid & 31;
+    for (uint32_t w = tid; w < 3 * D; w += kThreads) s_acc[w] = 0;
+    __syncthreads();
+    const KT* __restrict__ key = static_cast<const KT*>(sp.key_in[0]);
+    const VT* __restrict__ val = static_cast<const VT*>(sp.a_in[sum_slot]);
+    const int64_t lo = sp.lo[0];
+    const int64_t n = actual_rows(d_n, ncap);
+    // Each block owns a contiguous range of whole tiles and walks it segment by segment.
+    const int64_t chunk = cdiv(cdiv(n, gridDim.x), T) * T;
+    const int64_t cb = static_cast<int64_t>(blockIdx.x) * chunk;
+    const int64_t ce = n < cb + chunk ? n : cb + chunk;
+    int64_t pos = cb;
+    while (pos < ce) {
+        int q = 0;
+        int64_t qend = ce;
+        if (sp.nsegs > 1) {
+            q = seg_of(d_seg, sp.nsegs, pos);
+            if (q + 1 < sp.nsegs) {
+                const int64_t e = d_seg[q + 1];
+                if (e > pos && e < ce) qend = e;
+            }
+        }
+        // Tiles aligned to T, rows outside [pos, qend) masked: a tile that straddles
+        // a segment boundary is read once for each side.
+        for (int64_t tb = pos / T * T; tb < qend; tb += T) {
+            const int64_t r0 = tb + static_cast<int64_t>(tid) * ITEMS;
+            KT k[ITEMS];
+            VT v[ITEMS];
+            if (r0 + ITEMS <= ncap) {
+#pragma unroll
+                for (int c = 0; c < ITEMS * static_cast<int>(sizeof(KT)) / 16; ++c)
+                    reinterpret_cast<int4*>(k)[c] = reinterpret_cast<const int4*>(key + r0)[c];
+#pragma unroll
+                for (int c = 0; c < ITEMS * static_cast<int>(sizeof(VT)) / 16; ++c)
+                    reinterpret_cast<int4*>(v)[c] = reinterpret_cast<const int4*>(val + r0)[c];
+            } else {
+#pragma unroll
+                for (int i = 0; i < ITEMS; ++i) {
+                    k[i] = r0 + i < ncap ? key[r0 + i] : KT(0);
+                    v[i] = r0 + i < ncap ? val[r0 + i] : VT(0);
+                }
+            }
+            uint32_t idx[ITEMS];
+#pragma unroll
+            for (int i = 0; i < ITEMS; ++i) {
+                const int64_t r = r0 + i;
+                const uint64_t o = static_cast<uint64_t>(static_cast<int64_t>(k[i]) - lo);
+                idx[i] = r < pos || r >= qend ? kIdxNone : (o < D ? static_cast<uint32_t>(o) : kIdxOutside);
+            }
+#pragma unroll
+            for (int i = 0; i < ITEMS; ++i) {
+                const uint32_t c0 = __shfl_sync(FULL, idx[i], 0);
+                const uint32_t mm = __ballot_sync(FULL, idx[i] == c0);
+                uint64_t x = static_cast<uint64_t>(static_cast<int64_t>(v[i]));
+                uint32_t cnt = 1;
+                uint32_t d = idx[i];
+                if (c0 < kIdxOutside && __popc(mm) >= kMajority) {  // warp-uniform
+                    // Lane 0 (always in the group) applies the group's totals; the
+                    // group's other lanes drop out; lanes outside it keep their row.
+                    const bool in = (mm >> lane) & 1u;
+                    const uint64_t total = warp_sum_u64(in ? x : 0);
+                    if (lane == 0) {
+                        x = total;
+                        cnt = __popc(mm);
+                    } else if (in) {
+                        d = kIdxNone;
+                    }
+                }
+                if (d < kIdxOutside) {
+                    const uint32_t xl = static_cast<uint32_t>(x);
+                    const uint32_t old = atomicAdd(&s_lo[d], xl);
+                    const uint32_t h = static_cast<uint32_t>(x >> 32) + (old + xl < old ? 1u : 0u);
+                    if (h) red_add_shared(&s_hi[d], h);
+                    red_add_shared(&s_cnt[d], cnt);
+                } else if (d == kIdxOutside) {
+                    uint64_t full[2];
+                    full[sum_slot] = x;
+                    full[cnt_slot] = 1;
+                    global_add(g, sp, compose(sp, static_cast<int64_t>(k[i]), 0, q), full, max_groups, out_seg, status);
+                }
+            }
+        }
+        // Segment q's slots into the dense global array, then cleared for the next.
+        __syncthreads();
+        const uint64_t ebase = static_cast<uint64_t>(q) * D;
+        for (uint32_t d = tid; d < D; d += kThreads) {
+            const uint32_t c = s_cnt[d];
+            if (c) {
+                red_add_global(&sp.dg_acc[sum_slot * sp.E + ebase + d],
+                               (static_cast<unsigned long long>(s_hi[d]) << 32) | s_lo[d]);
+                red_add_global(&sp.dg_acc[cnt_slot * sp.E + ebase + d], c);
+                s_lo[d] = s_hi[d] = s_cnt[d] = 0;
+            }
+        }
+        __syncthreads();
+        pos = qend;
+    }
+}
+
+template <typename KT, typename VT>
+px_status launch_sum_count(const Spec& sp, int32_t sum_slot, int32_t cnt_slot, const int64_t* d_n, int64_t ncap,
+                           const int64_t* d_seg, const GTable& g, int64_t max_groups, int32_t* out_seg,
+                           int32_t* status, cudaStream_t st) {
+    constexpr int ITEMS = 16 / sizeof(KT) > 16 / sizeof(VT) ? 16 / sizeof(KT) : 16 / sizeof(VT);
+    auto kernel = groupby_sum_count_kernel<KT, VT, ITEMS>;
+    const size_t smem = 12 * static_cast<size_t>(sp.D);
+    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    // A block flushes its D slots at every segment end: give each at least 4 D rows.
+    const int64_t grid = std::max<int64_t>(
+        1, std::min<int64_t>(cdiv(ncap, std::max<int64_t>(kThreads * ITEMS, 4 * static_cast<int64_t>(sp.D))),
+                             sm_count()));
+    kernel<<<static_cast<unsigned>(grid), kThreads, smem, st>>>(sp, sum_slot, cnt_slot, d_n, ncap, d_seg, g,
+                                                              max_groups, out_seg, status);
+    note_launch();
+    return check_launch("px_groupby_agg sum-count");
+}
+
 constexpr int kEmitThreads = 256;
 constexpr int kEmitItems = 8;
 constexpr int kEmitTile = kEmitThreads * kEmitItems;
@@ -1074,7 +1214,34 @@ static px_status groupby_impl(const px_batch* in, const int32_t* key_cols, int32
     }
     const int64_t ncap = in->nrows;
     int32_t* status = &static_cast<WsHeader*>(d_ws)->status;
-    if (ncap > 0) {
+    // The lean kernel of the SUM + COUNT shape (see groupby_sum_count_kernel):
+    // one key of 4 or 8 bytes, a dense block mode with one replica of a dense
+    // global result, no selection, not fused with a probe.
+    int32_t sum_slot = -1, cnt_slot = -1;
+    if (naggs == 2)
+        for (int a = 0; a < 2; ++a) {
+            if (sp.op[a] == PX_COUNT) cnt_slot = a;
+            else if (sp.op[a] == PX_SUM && (sp.a_w[a] == 8 || sp.a_w[a] == 4)) sum_slot = a;
+        }
+    const bool sum_count = ncap > 0 && !probe && sp.dense && !sp.direct && sp.dglobal && sp.reps == 1 &&
+                           d_sel == nullptr && nkeys == 1 && (sp.key_w[0] == 4 || sp.key_w[0] == 8) &&
+                           sum_slot >= 0 && cnt_slot >= 0 && 12 * static_cast<size_t>(sp.D) <= kSmemBudget;
+    if (sum_count) {
+        const int64_t* d_n = in->d_nrows;
+        if (sp.key_w[0] == 4 && sp.a_w[sum_slot] == 8)
+            s = launch_sum_count<int32_t, int64_t>(sp, sum_slot, cnt_slot, d_n, ncap, d_seg, g, max_groups, d_out_seg,
+                                                   status, st);
+        else if (sp.key_w[0] == 4)
+            s = launch_sum_count<int32_t, int32_t>(sp, sum_slot, cnt_slot, d_n, ncap, d_seg, g, max_groups, d_out_seg,
+                                                   status, st);
+        else if (sp.a_w[sum_slot] == 8)
+            s = launch_sum_count<int64_t, int64_t>(sp, sum_slot, cnt_slot, d_n, ncap, d_seg, g, max_groups, d_out_seg,
+                                                   status, st);
+        else
+            s = launch_sum_count<int64_t, int32_t>(sp, sum_slot, cnt_slot, d_n, ncap, d_seg, g, max_groups, d_out_seg,
+                                                   status, st);
+        if (s != PX_OK) return s;
+    } else if (ncap > 0) {
         const int64_t* d_n = d_sel ? d_nsel : in->d_nrows;
         switch (naggs) {
             case 0: s = launch<0>(sp, smem, d_sel, d_n, ncap, d_seg, g, max_groups, d_out_seg, status, hslots, st); break;

@@ -409,3 +409,39 @@ def test_partition_every_launch_shape_gives_the_same_result(px):
         np.testing.assert_array_equal(host(off), woff)
         for c in range(3):
             np.testing.assert_array_equal(host(out[c]), want[c])
+
+
+@pytest.mark.parametrize("kt,vt", [(np.int32, np.int64), (np.int32, np.int32), (np.int64, np.int64),
+                                   (np.int64, np.int32)])
+def test_groupby_sum_count_wide_key_range(px, kt, vt):
+    """SUM + COUNT over a key range of 8193..16384 slots with a dense global result
+    and enough rows for dense block aggregation: the shape the lean sum-count kernel
+    serves (one shared-memory replica per block; the smaller input takes the direct
+    mode). Zipf-skewed keys (hot-key warp sums), keys outside the statistic (global
+    path), full-range values (carries into the high word, negatives), segments with
+    empty ones and boundaries off the tile grid, a ragged tail, and the reversed
+    aggregate order, all against the oracle."""
+    g = pxdata.rng(4200)
+    D = 8_500
+    for n in [4097, 5_500_003]:
+        ranks = pxdata.zipf_ranks(g, D, n, 1.1)
+        keys = (g.permutation(D)[ranks - 1] + 7).astype(kt)
+        out = g.random(n) < 0.001  # outside [7, 7 + D)
+        keys[out] = np.where(g.random(out.sum()) < 0.5, -5, D + 50).astype(kt)
+        vals = pxdata.random_column(g, n, vt)
+        cuts = np.sort(g.integers(0, n + 1, size=6))
+        seg = np.concatenate([[0], cuts[:2], cuts[2:3], cuts[2:3], cuts[3:], [n]]).astype(np.int64)
+        if kt == np.int64:  # a 64-bit key leaves no bits of the group code for segments
+            seg = np.array([0, n], np.int64)
+        for order in (0, 1):
+            o_aggs = [(oracle.SUM, vals, None), (oracle.COUNT, None, None)]
+            p_aggs = [(px.PX_SUM, 1, None), (px.PX_COUNT, None, None)]
+            if order:
+                o_aggs, p_aggs = o_aggs[::-1], p_aggs[::-1]
+            want = oracle.groupby([keys], o_aggs, seg=seg)
+            segmented = seg.size > 2
+            res = _gb(px, [keys, vals], [0], p_aggs, (seg.size - 1) * D + 64, seg=dev(seg) if segmented else None,
+                      key_range=[(7, 7 + D - 1)])
+            if not segmented:
+                want = oracle.groupby([keys], o_aggs)
+            assert_groups_equal(res, want, 1, segmented=segmented)
