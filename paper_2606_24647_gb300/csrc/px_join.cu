@@ -208,50 +208,31 @@ __device__ __forceinline__ void cursor_seek(SegCursor& c, const TableView& t, co
     c.g = seg_geom(t, c.q);
 }
 
-constexpr int kMatchWarps = kMatchThreads / 32;
-constexpr int kDeferCap = 32 + 32 * kMatchItems;  // fewer than 32 left over plus one tile's items
-
-// A lookup whose home bucket was full without its key, queued per warp so that
-// the rare walk on runs 32 keys at a time instead of stalling whole warps.
-struct Deferred {
-    int64_t j;        // probe position
-    int64_t key;
-    const Bucket* b;  // bucket read last
-    int32_t q;        // table segment
-    int32_t pad;
-};
-
-// Walks on from bucket e.b through the rest of its segment; records the build row
-// (or kNoMatch) of position e.j and counts a match in its tile.
-__device__ __forceinline__ void resolve_deferred(const TableView& t, const Deferred& e, int32_t* mrow,
-                                                 int32_t* tile_cnt) {
-    const SegGeom g = seg_geom(t, e.q);
-    const Bucket* segb = t.bk + g.b0;
-    const Bucket* b = e.b;
-    int32_t r = kNoMatch;
-    for (uint32_t round = 1; round < g.nb; ++round) {
-        b = b + 1 == segb + g.nb ? segb : b + 1;
+// Walks on from home bucket `hb` of a segment (a bucket full without the key)
+// through the following buckets: the key's build row, or kNoMatch at the first
+// empty slot. Occupied slots form a prefix of every probe sequence.
+__device__ __forceinline__ int32_t walk_on(const Bucket* segb, uint32_t nb, uint32_t hb, int64_t key) {
+    const Bucket* b = segb + hb;
+    for (uint32_t round = 1; round < nb; ++round) {
+        b = b + 1 == segb + nb ? segb : b + 1;
         const longlong2 k01 = *reinterpret_cast<const longlong2*>(&b->key[0]);
         const longlong2 k23 = *reinterpret_cast<const longlong2*>(&b->key[2]);
         bool end;
-        const int l = bucket_find(k01, k23, e.key, &end);
-        if (l >= 0) {
-            r = b->row[l];
-            break;
-        }
+        const int l = bucket_find(k01, k23, key, &end);
+        if (l >= 0) return b->row[l];
         if (end) break;
     }
-    mrow[e.j] = r;
-    if (r != kNoMatch) atomicAdd(&tile_cnt[e.j / kTile], 1);
+    return kNoMatch;
 }
 
 // Persistent over tiles (grid-stride), software-pipelined: the next tile's keys
 // are loaded while the current tile's buckets are in flight. No block-wide
 // barrier: every thread reads the (cached) table header once and follows its own
-// segment cursor; warps add their match counts atomically. Unique tables: every
-// position reads its home bucket's 4 keys (one sector), then the build row of a
-// match; the few keys whose bucket is full without them go to the warp's queue,
-// drained 32 at a time (and once more at the end).
+// segment cursor (one check per tile when all of the thread's positions lie in
+// its current segment); warps add their match counts atomically. Unique tables:
+// every position reads its home bucket's 4 keys (one sector), then the build row
+// of a match; the few keys whose home bucket is full without them walk on inline,
+// only in warps where some lane needs it.
 __global__ void __launch_bounds__(kMatchThreads, 2)
 probe_match_kernel(TableView t, int32_t S, const int64_t* __restrict__ fk, const int32_t* __restrict__ sel,
                    const int64_t* __restrict__ d_n, int64_t ncap, const int64_t* __restrict__ pseg,
@@ -276,9 +257,6 @@ probe_match_kernel(TableView t, int32_t S, const int64_t* __restrict__ fk, const
         return;
     }
     if (tile >= ntiles) return;
-    __shared__ Deferred s_def[kMatchWarps][kDeferCap];
-    Deferred* const dq = s_def[warp];
-    uint32_t nq = 0;  // entries in this warp's queue (warp-uniform)
     const uint32_t nv = static_cast<uint32_t>(n);  // positions with a key to look up
     SegCursor c;
     cursor_init(c, t, pseg, S, static_cast<uint32_t>(tile) * kTile + lane_off);
@@ -287,22 +265,29 @@ probe_match_kernel(TableView t, int32_t S, const int64_t* __restrict__ fk, const
     for (; tile < ntiles; tile += gridDim.x) {
         const uint32_t j0 = static_cast<uint32_t>(tile) * kTile + lane_off;
         int32_t out[kMatchItems];
-        uint32_t defer = 0;  // items queued for the walk on
-        int segq[kMatchItems];
+        SegGeom gi[kMatchItems];
+        if (static_cast<int64_t>(j0 + 32 * (kMatchItems - 1)) < c.end) {
+#pragma unroll
+            for (int i = 0; i < kMatchItems; ++i) gi[i] = c.g;
+        } else {
+#pragma unroll
+            for (int i = 0; i < kMatchItems; ++i) {
+                cursor_seek(c, t, pseg, S, j0 + 32 * i);
+                gi[i] = c.g;
+            }
+        }
         uint32_t hb[kMatchItems];  // home bucket, numbered within the segment
-        const Bucket* bp[kMatchItems];
 #pragma unroll
         for (int i = 0; i < kMatchItems; ++i) {
-            cursor_seek(c, t, pseg, S, j0 + 32 * i);
-            segq[i] = c.q;
-            hb[i] = home_bucket(static_cast<uint64_t>(keyv[i]), c.g.nb);
-            bp[i] = t.bk + c.g.b0 + hb[i];
+            hb[i] = home_bucket(static_cast<uint64_t>(keyv[i]), gi[i].nb);
             out[i] = kNoMatch;
         }
         if (unique) {
             longlong2 k01[kMatchItems], k23[kMatchItems];
+            const Bucket* bp[kMatchItems];
 #pragma unroll
             for (int i = 0; i < kMatchItems; ++i) {
+                bp[i] = t.bk + gi[i].b0 + hb[i];
                 if (keyv[i] != kEmpty) {
                     k01[i] = *reinterpret_cast<const longlong2*>(&bp[i]->key[0]);
                     k23[i] = *reinterpret_cast<const longlong2*>(&bp[i]->key[2]);
@@ -313,23 +298,19 @@ probe_match_kernel(TableView t, int32_t S, const int64_t* __restrict__ fk, const
             // Next tile's keys go out while this tile's buckets are in flight.
             int64_t keyn[kMatchItems];
             match_keys(fk, sel, nv, static_cast<uint32_t>(tile + gridDim.x) * kTile + lane_off, keyn);
+            uint32_t pend = 0;  // items whose home bucket is full without their key
 #pragma unroll
             for (int i = 0; i < kMatchItems; ++i) {
                 bool end;
                 const int l = bucket_find(k01[i], k23[i], keyv[i], &end);
                 const bool valid = keyv[i] != kEmpty;
                 if (valid && l >= 0) out[i] = bp[i]->row[l];
-                const bool d = valid && l < 0 && !end;
-                const uint32_t dm = __ballot_sync(FULL, d);
-                if (d) {
-                    Deferred& e = dq[nq + __popc(dm & lanemask_lt())];
-                    e.j = j0 + 32 * i;
-                    e.key = keyv[i];
-                    e.b = bp[i];
-                    e.q = segq[i];
-                    defer |= 1u << i;
-                }
-                nq += __popc(dm);
+                else if (valid && !end) pend |= 1u << i;
+            }
+            if (__any_sync(FULL, pend != 0)) {
+#pragma unroll
+                for (int i = 0; i < kMatchItems; ++i)
+                    if ((pend >> i) & 1u) out[i] = walk_on(t.bk + gi[i].b0, gi[i].nb, hb[i], keyv[i]);
             }
             uint32_t hits = 0;
 #pragma unroll
@@ -338,15 +319,6 @@ probe_match_kernel(TableView t, int32_t S, const int64_t* __restrict__ fk, const
                 keyv[i] = keyn[i];
             }
             if (lane == 0 && hits) atomicAdd(&tile_cnt[tile], static_cast<int32_t>(hits));  // zeroed before launch
-            if (nq >= 32) {
-                __syncwarp();
-                do {
-                    const Deferred e = dq[nq - 32 + lane];
-                    __syncwarp();
-                    resolve_deferred(t, e, mrow, tile_cnt);
-                    nq -= 32;
-                } while (nq >= 32);
-            }
         } else {
             // Multi-map: count every match; one match is recorded as its build row,
             // several as -(table slot of the first + 2) for the emit pass to walk.
@@ -354,12 +326,11 @@ probe_match_kernel(TableView t, int32_t S, const int64_t* __restrict__ fk, const
 #pragma unroll
             for (int i = 0; i < kMatchItems; ++i) {
                 if (keyv[i] == kEmpty) continue;
-                const SegGeom g = seg_geom(t, segq[i]);
-                const Bucket* segb = t.bk + g.b0;
+                const Bucket* segb = t.bk + gi[i].b0;
                 uint32_t first = 0;
-                const int32_t m = count_matches(segb, g.nb, 4 * hb[i], keyv[i], &first);
+                const int32_t m = count_matches(segb, gi[i].nb, 4 * hb[i], keyv[i], &first);
                 if (m == 1) out[i] = segb[first >> 2].row[first & 3];
-                else if (m > 1) out[i] = -static_cast<int32_t>(4 * g.b0 + first) - 2;
+                else if (m > 1) out[i] = -static_cast<int32_t>(4 * gi[i].b0 + first) - 2;
                 cnt += m;
             }
             match_keys(fk, sel, nv, static_cast<uint32_t>(tile + gridDim.x) * kTile + lane_off, keyv);
@@ -369,11 +340,9 @@ probe_match_kernel(TableView t, int32_t S, const int64_t* __restrict__ fk, const
 #pragma unroll
         for (int i = 0; i < kMatchItems; ++i) {
             const uint32_t j = j0 + 32 * i;
-            if (j < ncap && !((defer >> i) & 1u)) mrow[j] = out[i];
+            if (j < ncap) mrow[j] = out[i];
         }
     }
-    __syncwarp();
-    if (lane < static_cast<int>(nq)) resolve_deferred(t, dq[lane], mrow, tile_cnt);
 }
 
 constexpr int kScanThreads = 256;
@@ -446,6 +415,21 @@ probe_emit_kernel(TableView t, int32_t S, const int64_t* __restrict__ fk, const 
         const bool valid = lp[i] < rows;
         mr[i] = valid ? mrow[tb + lp[i]] : kNoMatch;
         prow[i] = valid ? (sel ? sel[tb + lp[i]] : static_cast<int32_t>(tb + lp[i])) : 0;
+    }
+    // The join's common shape (one 8-byte carried column, one 4-byte payload column):
+    // the carried values and the payload gathers are issued now, so their latency
+    // overlaps the ranking and the block combine below.
+    const bool early = oc.ncarry == 1 && oc.npay == 1 && oc.carry_w[0] == 8 && oc.pay_w[0] == 4;
+    int64_t cv[kItems];
+    int32_t pv[kItems];
+    if (early) {
+#pragma unroll
+        for (int i = 0; i < kItems; ++i) {
+            if (mr[i] >= 0) {
+                cv[i] = static_cast<const int64_t*>(oc.carry_in[0])[prow[i]];
+                pv[i] = static_cast<const int32_t*>(oc.pay_in[0])[mr[i]];
+            }
+        }
     }
     // Output rows in position order (warp, item, lane). Unique matches count 0 or 1,
     // so a ballot per item ranks them; a warp holding a multi-map position (several
@@ -528,8 +512,19 @@ probe_emit_kernel(TableView t, int32_t S, const int64_t* __restrict__ fk, const 
         for (int i = 0; i < kItems; ++i)
             if (one[i]) build_row[pos[i]] = mr[i];
     }
-    for (int c = 0; c < oc.ncarry; ++c) gather_store(oc.carry_w[c], oc.carry_in[c], oc.carry_out[c], prow, pos, one);
-    for (int c = 0; c < oc.npay; ++c) gather_store(oc.pay_w[c], oc.pay_in[c], oc.pay_out[c], mr, pos, one);
+    if (early) {
+#pragma unroll
+        for (int i = 0; i < kItems; ++i) {
+            if (one[i]) {
+                static_cast<int64_t*>(oc.carry_out[0])[pos[i]] = cv[i];
+                static_cast<int32_t*>(oc.pay_out[0])[pos[i]] = pv[i];
+            }
+        }
+    } else {
+        for (int c = 0; c < oc.ncarry; ++c)
+            gather_store(oc.carry_w[c], oc.carry_in[c], oc.carry_out[c], prow, pos, one);
+        for (int c = 0; c < oc.npay; ++c) gather_store(oc.pay_w[c], oc.pay_in[c], oc.pay_out[c], mr, pos, one);
+    }
     if (!multi) return;
     // Positions with several matches: walk the chain again, emitting each.
 #pragma unroll
