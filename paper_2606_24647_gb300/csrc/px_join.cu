@@ -174,29 +174,38 @@ __device__ __forceinline__ int32_t count_matches(const Bucket* segb, uint32_t nb
 constexpr int kMatchThreads = 512;
 constexpr int kMatchItems = kTile / kMatchThreads;  // positions per thread per tile (same tiles as emit)
 
-// Keys of this thread's positions of tile `tile` (kEmpty where there is no row).
+// Keys of this thread's positions of the tile whose first position is j0 (kEmpty
+// where there is no row).
+template <bool kSel>
 __device__ __forceinline__ void match_keys(const int64_t* __restrict__ fk, const int32_t* __restrict__ sel,
                                            uint32_t n, uint32_t j0, int64_t* keyv) {
 #pragma unroll
     for (int i = 0; i < kMatchItems; ++i) {
         const uint32_t j = j0 + 32 * i;
-        keyv[i] = j < n ? fk[sel ? static_cast<int64_t>(sel[j]) : j] : kEmpty;
+        keyv[i] = j < n ? fk[kSel ? static_cast<uint32_t>(sel[j]) : j] : kEmpty;
     }
 }
 
 // Segment cursor of one thread: segment q holds the thread's latest position,
-// `end` is where q's positions end, g locates q's buckets. A thread's positions
+// `end` is where q's positions end, segb/nb are q's buckets. A thread's positions
 // only increase, so the cursor only moves forward.
 struct SegCursor {
     int q;
     int64_t end;
-    SegGeom g;
+    const Bucket* segb;
+    uint32_t nb;
 };
+
+__device__ __forceinline__ void cursor_geom(SegCursor& c, const TableView& t) {
+    const SegGeom g = seg_geom(t, c.q);
+    c.segb = t.bk + g.b0;
+    c.nb = g.nb;
+}
 
 __device__ __forceinline__ void cursor_init(SegCursor& c, const TableView& t, const int64_t* pseg, int S, int64_t j) {
     c.q = S > 1 ? seg_of(pseg, S, j) : 0;
     c.end = c.q + 1 < S ? pseg[c.q + 1] : INT64_MAX;
-    c.g = seg_geom(t, c.q);
+    cursor_geom(c, t);
 }
 
 __device__ __forceinline__ void cursor_seek(SegCursor& c, const TableView& t, const int64_t* pseg, int S, int64_t j) {
@@ -205,7 +214,7 @@ __device__ __forceinline__ void cursor_seek(SegCursor& c, const TableView& t, co
         ++c.q;
         c.end = c.q + 1 < S ? pseg[c.q + 1] : INT64_MAX;
     } while (j >= c.end);
-    c.g = seg_geom(t, c.q);
+    cursor_geom(c, t);
 }
 
 // Walks on from home bucket `hb` of a segment (a bucket full without the key)
@@ -225,19 +234,33 @@ __device__ __forceinline__ int32_t walk_on(const Bucket* segb, uint32_t nb, uint
     return kNoMatch;
 }
 
+// Unique table, one home bucket: the build row of `key` among the bucket's keys
+// k01, k23 and rows rv, else kNoMatch. A unique table holds a key at most once,
+// so the four compares select without ordering.
+__device__ __forceinline__ int32_t unique_pick(longlong2 k01, longlong2 k23, int4 rv, int64_t key) {
+    int32_t r = kNoMatch;
+    r = k01.x == key ? rv.x : r;
+    r = k01.y == key ? rv.y : r;
+    r = k23.x == key ? rv.z : r;
+    r = k23.y == key ? rv.w : r;
+    return r;
+}
+
 // Persistent over tiles (grid-stride), software-pipelined: the next tile's keys
 // are loaded while the current tile's buckets are in flight. No block-wide
 // barrier: every thread reads the (cached) table header once and follows its own
 // segment cursor (one check per tile when all of the thread's positions lie in
 // its current segment); warps add their match counts atomically. Unique tables:
-// every position reads its home bucket's 4 keys (one sector), then the build row
-// of a match; the few keys whose home bucket is full without them walk on inline,
-// only in warps where some lane needs it.
+// every position reads its home bucket's keys and rows (two sectors, one round
+// trip); the few keys whose home bucket is full without them walk on inline,
+// only in warps where some lane needs it. Only positions below the row count are
+// written: the emit reads no other.
+template <bool kSel>
 __global__ void __launch_bounds__(kMatchThreads, 2)
 probe_match_kernel(TableView t, int32_t S, const int64_t* __restrict__ fk, const int32_t* __restrict__ sel,
                    const int64_t* __restrict__ d_n, int64_t ncap, const int64_t* __restrict__ pseg,
                    int32_t* __restrict__ mrow, int32_t* __restrict__ tile_cnt, int32_t* status, int32_t npay,
-                   int64_t payload_rows, int64_t ntiles) {
+                   int64_t payload_rows, uint32_t ntiles) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t n = actual_rows(d_n, ncap);
     const bool bad = t.hdr->magic != kMagic || t.hdr->nsegs != S || (npay > 0 && t.hdr->nbuild > payload_rows);
@@ -246,101 +269,101 @@ probe_match_kernel(TableView t, int32_t S, const int64_t* __restrict__ fk, const
     // Positions fit 32 bits (batches hold at most INT32_MAX rows); item i of a tile
     // sits at tile * kTile + lane_off + 32 i.
     const uint32_t lane_off = warp * (32 * kMatchItems) + lane;
-    int64_t tile = blockIdx.x;
+    const uint32_t nv = static_cast<uint32_t>(n);  // positions with a key to look up
+    uint32_t tile = blockIdx.x;
     if (bad) {  // a table this call cannot use: no matches, and no reads past its header
         for (; tile < ntiles; tile += gridDim.x)
 #pragma unroll
             for (int i = 0; i < kMatchItems; ++i) {
-                const int64_t j = tile * kTile + lane_off + 32 * i;
-                if (j < ncap) mrow[j] = kNoMatch;
+                const uint32_t j = tile * kTile + lane_off + 32 * i;
+                if (j < nv) mrow[j] = kNoMatch;
             }
         return;
     }
     if (tile >= ntiles) return;
-    const uint32_t nv = static_cast<uint32_t>(n);  // positions with a key to look up
     SegCursor c;
-    cursor_init(c, t, pseg, S, static_cast<uint32_t>(tile) * kTile + lane_off);
+    cursor_init(c, t, pseg, S, tile * kTile + lane_off);
     int64_t keyv[kMatchItems];
-    match_keys(fk, sel, nv, static_cast<uint32_t>(tile) * kTile + lane_off, keyv);
+    match_keys<kSel>(fk, sel, nv, tile * kTile + lane_off, keyv);
     for (; tile < ntiles; tile += gridDim.x) {
-        const uint32_t j0 = static_cast<uint32_t>(tile) * kTile + lane_off;
-        int32_t out[kMatchItems];
-        SegGeom gi[kMatchItems];
+        const uint32_t j0 = tile * kTile + lane_off;
+        const Bucket* segb[kMatchItems];
+        uint32_t nb[kMatchItems];
         if (static_cast<int64_t>(j0 + 32 * (kMatchItems - 1)) < c.end) {
 #pragma unroll
-            for (int i = 0; i < kMatchItems; ++i) gi[i] = c.g;
+            for (int i = 0; i < kMatchItems; ++i) {
+                segb[i] = c.segb;
+                nb[i] = c.nb;
+            }
         } else {
 #pragma unroll
             for (int i = 0; i < kMatchItems; ++i) {
                 cursor_seek(c, t, pseg, S, j0 + 32 * i);
-                gi[i] = c.g;
+                segb[i] = c.segb;
+                nb[i] = c.nb;
             }
         }
         uint32_t hb[kMatchItems];  // home bucket, numbered within the segment
 #pragma unroll
-        for (int i = 0; i < kMatchItems; ++i) {
-            hb[i] = home_bucket(static_cast<uint64_t>(keyv[i]), gi[i].nb);
-            out[i] = kNoMatch;
-        }
+        for (int i = 0; i < kMatchItems; ++i) hb[i] = home_bucket(static_cast<uint64_t>(keyv[i]), nb[i]);
+        int32_t out[kMatchItems];
+        int32_t cnt = 0;
         if (unique) {
+            // Every bucket is read whole (keys and rows): hb < nb keeps the reads
+            // inside the segment even for positions without a key.
             longlong2 k01[kMatchItems], k23[kMatchItems];
-            const Bucket* bp[kMatchItems];
+            int4 rv[kMatchItems];
 #pragma unroll
             for (int i = 0; i < kMatchItems; ++i) {
-                bp[i] = t.bk + gi[i].b0 + hb[i];
-                if (keyv[i] != kEmpty) {
-                    k01[i] = *reinterpret_cast<const longlong2*>(&bp[i]->key[0]);
-                    k23[i] = *reinterpret_cast<const longlong2*>(&bp[i]->key[2]);
-                } else {
-                    k01[i] = k23[i] = make_longlong2(kEmpty, kEmpty);
-                }
+                const Bucket* b = segb[i] + hb[i];
+                const longlong4_32a k = *reinterpret_cast<const longlong4_32a*>(&b->key[0]);  // one 32-byte load
+                k01[i] = make_longlong2(k.x, k.y);
+                k23[i] = make_longlong2(k.z, k.w);
+                rv[i] = *reinterpret_cast<const int4*>(&b->row[0]);
             }
             // Next tile's keys go out while this tile's buckets are in flight.
             int64_t keyn[kMatchItems];
-            match_keys(fk, sel, nv, static_cast<uint32_t>(tile + gridDim.x) * kTile + lane_off, keyn);
+            match_keys<kSel>(fk, sel, nv, (tile + gridDim.x) * kTile + lane_off, keyn);
             uint32_t pend = 0;  // items whose home bucket is full without their key
 #pragma unroll
             for (int i = 0; i < kMatchItems; ++i) {
-                bool end;
-                const int l = bucket_find(k01[i], k23[i], keyv[i], &end);
-                const bool valid = keyv[i] != kEmpty;
-                if (valid && l >= 0) out[i] = bp[i]->row[l];
-                else if (valid && !end) pend |= 1u << i;
+                const bool live = keyv[i] != kEmpty;  // a row, and not the reserved key
+                const int32_t r = unique_pick(k01[i], k23[i], rv[i], keyv[i]);
+                out[i] = live ? r : kNoMatch;
+                if (live && r < 0 && k23[i].y != kEmpty) pend |= 1u << i;
             }
             if (__any_sync(FULL, pend != 0)) {
 #pragma unroll
                 for (int i = 0; i < kMatchItems; ++i)
-                    if ((pend >> i) & 1u) out[i] = walk_on(t.bk + gi[i].b0, gi[i].nb, hb[i], keyv[i]);
+                    if ((pend >> i) & 1u) out[i] = walk_on(segb[i], nb[i], hb[i], keyv[i]);
             }
-            uint32_t hits = 0;
 #pragma unroll
             for (int i = 0; i < kMatchItems; ++i) {
-                hits += __popc(__ballot_sync(FULL, out[i] != kNoMatch));
+                cnt += out[i] >= 0 ? 1 : 0;
                 keyv[i] = keyn[i];
             }
-            if (lane == 0 && hits) atomicAdd(&tile_cnt[tile], static_cast<int32_t>(hits));  // zeroed before launch
         } else {
             // Multi-map: count every match; one match is recorded as its build row,
             // several as -(table slot of the first + 2) for the emit pass to walk.
-            int32_t cnt = 0;
 #pragma unroll
             for (int i = 0; i < kMatchItems; ++i) {
+                out[i] = kNoMatch;
                 if (keyv[i] == kEmpty) continue;
-                const Bucket* segb = t.bk + gi[i].b0;
                 uint32_t first = 0;
-                const int32_t m = count_matches(segb, gi[i].nb, 4 * hb[i], keyv[i], &first);
-                if (m == 1) out[i] = segb[first >> 2].row[first & 3];
-                else if (m > 1) out[i] = -static_cast<int32_t>(4 * gi[i].b0 + first) - 2;
+                const int32_t m = count_matches(segb[i], nb[i], 4 * hb[i], keyv[i], &first);
+                const int64_t b0 = segb[i] - t.bk;
+                if (m == 1) out[i] = segb[i][first >> 2].row[first & 3];
+                else if (m > 1) out[i] = -static_cast<int32_t>(4 * b0 + first) - 2;
                 cnt += m;
             }
-            match_keys(fk, sel, nv, static_cast<uint32_t>(tile + gridDim.x) * kTile + lane_off, keyv);
-            cnt = warp_sum(cnt);
-            if (lane == 0 && cnt) atomicAdd(&tile_cnt[tile], cnt);  // tile_cnt zeroed before the launch
+            match_keys<kSel>(fk, sel, nv, (tile + gridDim.x) * kTile + lane_off, keyv);
         }
+        cnt = static_cast<int32_t>(__reduce_add_sync(FULL, static_cast<uint32_t>(cnt)));
+        if (lane == 0 && cnt) atomicAdd(&tile_cnt[tile], cnt);  // zeroed before the launch
 #pragma unroll
         for (int i = 0; i < kMatchItems; ++i) {
             const uint32_t j = j0 + 32 * i;
-            if (j < ncap) mrow[j] = out[i];
+            if (j < nv) mrow[j] = out[i];
         }
     }
 }
@@ -392,21 +415,26 @@ probe_scan_kernel(const int32_t* __restrict__ cnt, int64_t* __restrict__ off, in
         run += v[k];
     }
 }
+// Output rows of one tile in position order. A tile whose every position matched
+// exactly once in a unique table (its count equals its rows) writes output row
+// tile_off + position - tile start, with no ranking. Other tiles rank their
+// matches: unique matches count 0 or 1, so a ballot per item ranks them; a warp
+// holding a multi-map position (several matches, counted again along its chain)
+// takes shuffle scans instead.
+template <bool kSel>
 __global__ void __launch_bounds__(kThreads)
 probe_emit_kernel(TableView t, int32_t S, const int64_t* __restrict__ fk, const int32_t* __restrict__ sel,
                   const int64_t* __restrict__ d_n, int64_t ncap, const int64_t* __restrict__ pseg,
-                  const int32_t* __restrict__ mrow, const int64_t* __restrict__ tile_off, OutCols oc,
-                  int32_t* __restrict__ probe_row, int32_t* __restrict__ build_row, int64_t out_cap,
-                  int64_t* __restrict__ d_out_seg) {
+                  const int32_t* __restrict__ mrow, const int32_t* __restrict__ tile_cnt,
+                  const int64_t* __restrict__ tile_off, OutCols oc, int32_t* __restrict__ probe_row,
+                  int32_t* __restrict__ build_row, int64_t out_cap) {
     __shared__ int32_t s_warp[kWarps];
-    __shared__ int32_t s_q0;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t n = actual_rows(d_n, ncap);
     // Positions fit 32 bits (batches hold at most INT32_MAX rows).
     const uint32_t tb = static_cast<uint32_t>(blockIdx.x) * kTile;
     const int rows = n - tb >= kTile ? kTile : static_cast<int>(n - tb);  // valid positions in this tile (<= 0: none)
-    // One thread finds the segment of the tile's first position for everyone.
-    if (d_out_seg && threadIdx.x == 0) s_q0 = (S > 1 && rows > 0) ? seg_of(pseg, S, tb) : 0;
+    if (rows <= 0) return;
     int lp[kItems];  // position within the tile
     int32_t mr[kItems], prow[kItems];
 #pragma unroll
@@ -414,7 +442,7 @@ probe_emit_kernel(TableView t, int32_t S, const int64_t* __restrict__ fk, const 
         lp[i] = warp * (32 * kItems) + i * 32 + lane;
         const bool valid = lp[i] < rows;
         mr[i] = valid ? mrow[tb + lp[i]] : kNoMatch;
-        prow[i] = valid ? (sel ? sel[tb + lp[i]] : static_cast<int32_t>(tb + lp[i])) : 0;
+        prow[i] = valid ? (kSel ? sel[tb + lp[i]] : static_cast<int32_t>(tb + lp[i])) : 0;
     }
     // The join's common shape (one 8-byte carried column, one 4-byte payload column):
     // the carried values and the payload gathers are issued now, so their latency
@@ -431,75 +459,65 @@ probe_emit_kernel(TableView t, int32_t S, const int64_t* __restrict__ fk, const 
             }
         }
     }
-    // Output rows in position order (warp, item, lane). Unique matches count 0 or 1,
-    // so a ballot per item ranks them; a warp holding a multi-map position (several
-    // matches, counted again along its chain) takes shuffle scans instead.
-    bool has_multi = false;
-#pragma unroll
-    for (int i = 0; i < kItems; ++i) has_multi |= mr[i] < kNoMatch;
-    const bool multi = __any_sync(FULL, has_multi);
-    int32_t m[kItems], pre[kItems];
-    int64_t key[kItems];
-    int32_t wsum = 0;
-    if (!multi) {
-        const uint32_t lt = lanemask_lt();
-#pragma unroll
-        for (int i = 0; i < kItems; ++i) {
-            m[i] = mr[i] >= 0 ? 1 : 0;
-            key[i] = 0;
-            const uint32_t b = __ballot_sync(FULL, m[i] != 0);
-            pre[i] = wsum + __popc(b & lt);
-            wsum += __popc(b);
-        }
-    } else {
-#pragma unroll
-        for (int i = 0; i < kItems; ++i) {
-            m[i] = mr[i] >= 0 ? 1 : 0;
-            key[i] = 0;
-            if (mr[i] < kNoMatch) {
-                const SegGeom g = seg_geom(t, S > 1 ? seg_of(pseg, S, tb + lp[i]) : 0);
-                const uint32_t first = static_cast<uint32_t>(-static_cast<int64_t>(mr[i]) - 2 - 4 * g.b0);
-                key[i] = fk[prow[i]];
-                uint32_t dummy = 0;
-                m[i] = count_matches(t.bk + g.b0, g.nb, first, key[i], &dummy);
-            }
-            const int32_t incl = warp_incl_scan(m[i]);
-            pre[i] = wsum + incl - m[i];
-            wsum += __shfl_sync(FULL, incl, 31);
-        }
-    }
-    // Block combine; the tile's first row comes from the scan of the tile counts.
-    if (lane == 0) s_warp[warp] = wsum;
-    __syncthreads();
-    int32_t wb = lane < warp ? s_warp[lane] : 0;  // totals of the warps before this one, in lanes < kWarps
-#pragma unroll
-    for (int d = 1; d < kWarps; d <<= 1) wb += __shfl_xor_sync(FULL, wb, d);
-    wb = __shfl_sync(FULL, wb, 0);
-    const int64_t base = tile_off[blockIdx.x] + wb;
+    const int64_t tile_base = tile_off[blockIdx.x];
     int64_t pos[kItems];
     bool one[kItems];
-#pragma unroll
-    for (int i = 0; i < kItems; ++i) {
-        pos[i] = base + pre[i];
-        one[i] = mr[i] >= 0 && pos[i] < out_cap;
-    }
-    if (d_out_seg) {
-        // A position where segments start (several when some are empty) gives those
-        // segments their first output row; a forward cursor over the segment starts.
-        int q = s_q0;
-        int64_t start = S > 1 ? pseg[q] : 0;
-        int64_t end = q + 1 < S ? pseg[q + 1] : INT64_MAX;
+    int32_t m[kItems];
+    int64_t key[kItems];
+    bool multi = false;
+    if (tile_cnt[blockIdx.x] == rows && t.hdr->unique != 0) {
+        // Every position of the tile matched once: no ranking, no block combine.
+        const int64_t room = out_cap - tile_base;  // output rows left from this tile's first
 #pragma unroll
         for (int i = 0; i < kItems; ++i) {
-            if (lp[i] >= rows) continue;
-            const int64_t j = tb + lp[i];
-            while (j >= end) {
-                ++q;
-                start = end;
-                end = q + 1 < S ? pseg[q + 1] : INT64_MAX;
+            pos[i] = tile_base + lp[i];
+            one[i] = lp[i] < rows && lp[i] < room;
+        }
+    } else {
+        bool has_multi = false;
+#pragma unroll
+        for (int i = 0; i < kItems; ++i) has_multi |= mr[i] < kNoMatch;
+        multi = __any_sync(FULL, has_multi);
+        int32_t pre[kItems];
+        int32_t wsum = 0;
+        if (!multi) {
+            const uint32_t lt = lanemask_lt();
+#pragma unroll
+            for (int i = 0; i < kItems; ++i) {
+                m[i] = mr[i] >= 0 ? 1 : 0;
+                const uint32_t b = __ballot_sync(FULL, m[i] != 0);
+                pre[i] = wsum + __popc(b & lt);
+                wsum += __popc(b);
             }
-            if (j == start)
-                for (int r = q; r >= 0 && (S > 1 ? pseg[r] == j : j == 0); --r) d_out_seg[r] = pos[i];
+        } else {
+#pragma unroll
+            for (int i = 0; i < kItems; ++i) {
+                m[i] = mr[i] >= 0 ? 1 : 0;
+                key[i] = 0;
+                if (mr[i] < kNoMatch) {
+                    const SegGeom g = seg_geom(t, S > 1 ? seg_of(pseg, S, tb + lp[i]) : 0);
+                    const uint32_t first = static_cast<uint32_t>(-static_cast<int64_t>(mr[i]) - 2 - 4 * g.b0);
+                    key[i] = fk[prow[i]];
+                    uint32_t dummy = 0;
+                    m[i] = count_matches(t.bk + g.b0, g.nb, first, key[i], &dummy);
+                }
+                const int32_t incl = warp_incl_scan(m[i]);
+                pre[i] = wsum + incl - m[i];
+                wsum += __shfl_sync(FULL, incl, 31);
+            }
+        }
+        // Block combine; the tile's first row comes from the scan of the tile counts.
+        if (lane == 0) s_warp[warp] = wsum;
+        __syncthreads();
+        int32_t wb = lane < warp ? s_warp[lane] : 0;  // totals of the warps before this one, in lanes < kWarps
+#pragma unroll
+        for (int d = 1; d < kWarps; d <<= 1) wb += __shfl_xor_sync(FULL, wb, d);
+        wb = __shfl_sync(FULL, wb, 0);
+        const int64_t base = tile_base + wb;
+#pragma unroll
+        for (int i = 0; i < kItems; ++i) {
+            pos[i] = base + pre[i];
+            one[i] = mr[i] >= 0 && pos[i] < out_cap;
         }
     }
     if (probe_row) {
@@ -548,14 +566,45 @@ probe_emit_kernel(TableView t, int32_t S, const int64_t* __restrict__ fk, const 
     }
 }
 
-// Segment starts at or past the end of the positions: out_seg[q] = nout.
-__global__ void probe_seg_tail_kernel(const int64_t* __restrict__ pseg, int32_t S, int32_t segmented,
-                                      const int64_t* __restrict__ d_n, int64_t ncap, const int64_t* __restrict__ d_nout,
-                                      int64_t* __restrict__ d_out_seg) {
+// First output row of every segment (out_seg[q], q in [0, S]): the output rows of
+// the positions before the segment's first position, i.e. its tile's first output
+// row plus the matches of the tile's positions before it; nout for a segment that
+// starts at or past the last position. One block per segment, one thread per
+// position of the tile.
+__global__ void __launch_bounds__(kTile)
+probe_seg_kernel(TableView t, int32_t S, int32_t segmented, const int64_t* __restrict__ pseg,
+                 const int64_t* __restrict__ fk, const int32_t* __restrict__ sel, const int64_t* __restrict__ d_n,
+                 int64_t ncap, const int32_t* __restrict__ mrow, const int64_t* __restrict__ tile_off,
+                 const int64_t* __restrict__ d_nout, int64_t* __restrict__ d_out_seg) {
+    __shared__ int32_t s_warp[kTile / 32];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t q = blockIdx.x;
     const int64_t n = actual_rows(d_n, ncap);
-    for (int q = threadIdx.x; q <= S; q += blockDim.x) {
-        const int64_t start = segmented ? pseg[q] : (q == 0 ? 0 : n);
-        if (start >= n) d_out_seg[q] = *d_nout;
+    int64_t start = segmented ? pseg[q] : (q == 0 ? 0 : n);
+    start = start < 0 ? 0 : start;
+    if (start >= n) {
+        if (threadIdx.x == 0) d_out_seg[q] = *d_nout;
+        return;
+    }
+    const int64_t j = start / kTile * kTile + threadIdx.x;
+    int32_t cnt = 0;
+    if (j < start) {
+        const int32_t r = mrow[j];
+        if (r >= 0) {
+            cnt = 1;
+        } else if (r < kNoMatch) {  // first of several matches: count them along the chain
+            const SegGeom g = seg_geom(t, S > 1 ? seg_of(pseg, S, j) : 0);
+            const uint32_t first = static_cast<uint32_t>(-static_cast<int64_t>(r) - 2 - 4 * g.b0);
+            uint32_t dummy = 0;
+            cnt = count_matches(t.bk + g.b0, g.nb, first, fk[sel ? static_cast<int64_t>(sel[j]) : j], &dummy);
+        }
+    }
+    cnt = static_cast<int32_t>(__reduce_add_sync(FULL, static_cast<uint32_t>(cnt)));
+    if (lane == 0) s_warp[warp] = cnt;
+    __syncthreads();
+    if (warp == 0) {
+        cnt = static_cast<int32_t>(__reduce_add_sync(FULL, static_cast<uint32_t>(s_warp[lane])));
+        if (lane == 0) d_out_seg[q] = tile_off[start / kTile] + cnt;
     }
 }
 
@@ -589,7 +638,7 @@ extern "C" {
 size_t px_join_table_bytes(int64_t nbuild, int32_t nsegs) {
     if (nbuild < 0) nbuild = 0;
     const int32_t S = nsegs > 0 ? nsegs : 1;
-    return 64 + seg_area_bytes(S) + static_cast<size_t>(table_buckets(nbuild, S)) * sizeof(Bucket);
+    return 64 + seg_area_bytes(S) + 48 + static_cast<size_t>(table_buckets(nbuild, S)) * sizeof(Bucket);
 }
 
 size_t px_join_build_ws_bytes(int64_t nbuild) {
@@ -711,11 +760,13 @@ px_status px_join_probe(const void* d_table, const px_batch* probe, int32_t fk_c
     const int64_t* fk = static_cast<const int64_t*>(probe->cols[fk_col].data);
     const unsigned grid = static_cast<unsigned>(L.ntiles);
     cudaMemsetAsync(tcnt, 0, 4 * static_cast<size_t>(L.ntiles), st);
+    const bool has_sel = d_sel != nullptr;
+    const auto match = has_sel ? probe_match_kernel<true> : probe_match_kernel<false>;
     int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, probe_match_kernel, kMatchThreads, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, match, kMatchThreads, 0);
     const unsigned mgrid = static_cast<unsigned>(std::min<int64_t>(L.ntiles, int64_t(sm_count()) * std::max(1, per_sm)));
-    probe_match_kernel<<<mgrid, kMatchThreads, 0, st>>>(t, S, fk, d_sel, d_n, ncap, d_seg, mrow, tcnt, status, npay,
-                                                        build_payload ? build_payload->nrows : 0, L.ntiles);
+    match<<<mgrid, kMatchThreads, 0, st>>>(t, S, fk, d_sel, d_n, ncap, d_seg, mrow, tcnt, status, npay,
+                                           build_payload ? build_payload->nrows : 0, static_cast<uint32_t>(L.ntiles));
     note_launch();
     if ((s = check_launch("px_join_probe match")) != PX_OK) return s;
     cudaMemsetAsync(ws + L.scan, 0, scan_scratch_bytes(L.nscan), st);
@@ -723,12 +774,14 @@ px_status px_join_probe(const void* d_table, const px_batch* probe, int32_t fk_c
         tcnt, toff, L.ntiles, out->nrows, d_nout, scan_scratch(ws + L.scan), status, L.nscan);
     note_launch();
     if ((s = check_launch("px_join_probe scan")) != PX_OK) return s;
-    probe_emit_kernel<<<grid, kThreads, 0, st>>>(t, S, fk, d_sel, d_n, ncap, d_seg, mrow, toff, oc, d_probe_row,
-                                                 d_build_row, out->nrows, d_out_seg);
+    const auto emit = has_sel ? probe_emit_kernel<true> : probe_emit_kernel<false>;
+    emit<<<grid, kThreads, 0, st>>>(t, S, fk, d_sel, d_n, ncap, d_seg, mrow, tcnt, toff, oc, d_probe_row,
+                                    d_build_row, out->nrows);
     note_launch();
     if ((s = check_launch("px_join_probe emit")) != PX_OK) return s;
     if (d_out_seg) {
-        probe_seg_tail_kernel<<<1, 256, 0, st>>>(d_seg, S, nsegs > 0 ? 1 : 0, d_n, ncap, d_nout, d_out_seg);
+        probe_seg_kernel<<<static_cast<unsigned>(S + 1), kTile, 0, st>>>(t, S, nsegs > 0 ? 1 : 0, d_seg, fk, d_sel, d_n, ncap, mrow, toff,
+                                                     d_nout, d_out_seg);
         note_launch();
         if ((s = check_launch("px_join_probe segments")) != PX_OK) return s;
     }

@@ -2,8 +2,11 @@
 // pipelines (px_fragments.cu). The table is caller memory:
 //   [0, 64)            header: magic, nsegs, unique flag, build rows
 //   [64, 64 + A)       copy of the build segment offsets (nsegs + 1 int64)
-//   [64 + A, ...)      buckets of 64 bytes: 4 int64 keys, their 4 int32 build
-//                      rows, 16 bytes of padding
+//   [64 + A + p, ...)  buckets of 64 bytes: 4 int64 keys, their 4 int32 build
+//                      rows, 16 bytes of padding; p < 64 pads the first bucket
+//                      to a 64-byte address (the caller's table is only 16-byte
+//                      aligned), so 32-byte vector loads of a bucket's keys are
+//                      aligned
 // Segment q of n_q rows owns buckets [b_q, b_{q+1}) with b_q = floor(seg[q] / 2) + q
 // (at least 2 n_q + 2 slots: load factor < 1/2). Slots are numbered
 // 4 * bucket + lane; linear probing over slots starts at the first slot of the
@@ -46,7 +49,8 @@ inline TableView table_view(void* d_table, int32_t S) {
     char* b = static_cast<char*>(d_table);
     t.hdr = reinterpret_cast<TableHeader*>(b);
     t.seg = reinterpret_cast<int64_t*>(b + 64);
-    t.bk = reinterpret_cast<Bucket*>(b + 64 + seg_area_bytes(S));
+    const uintptr_t bk = reinterpret_cast<uintptr_t>(b + 64 + seg_area_bytes(S));
+    t.bk = reinterpret_cast<Bucket*>((bk + 63) & ~static_cast<uintptr_t>(63));
     return t;
 }
 

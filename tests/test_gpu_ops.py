@@ -146,6 +146,48 @@ def test_join_unique_parity(px):
             np.testing.assert_array_equal(host(res["cols"][1], m), attr[br])
 
 
+def test_join_full_tiles_next_to_partial_tiles(px):
+    # every position of the first tiles matches (ranked without ballots), then
+    # tiles with misses, then a selection that makes every tile partial again
+    g = pxdata.rng(309)
+    pk = g.permutation(50_000).astype(np.int64)
+    fk = np.concatenate([pk[g.integers(0, pk.size, 40_960)],
+                         pxdata.random_column(g, 30_001, np.int64, -20_000, 70_000),
+                         pk[g.integers(0, pk.size, 5_000)]])
+    for sel in [None, oracle.filter(pxdata.random_column(g, fk.size, np.int32, 0, 9), 0, 7)]:
+        res, attr, amount, ws = _join(px, pk, fk, sel=sel)
+        assert ws.status() == px.PX_OK
+        pr, br, _ = oracle.join(pk, fk, sel=sel)
+        m = count(res["nout"])
+        assert m == pr.size
+        np.testing.assert_array_equal(host(res["probe_row"], m), pr)
+        np.testing.assert_array_equal(host(res["build_row"], m), br)
+        np.testing.assert_array_equal(host(res["cols"][0], m), amount[pr])
+        np.testing.assert_array_equal(host(res["cols"][1], m), attr[br])
+
+
+def test_join_table_at_a_16_byte_offset(px):
+    # the table is caller memory aligned to 16 bytes only; its buckets are padded
+    # to 64-byte addresses inside it
+    g = pxdata.rng(310)
+    pk = g.permutation(30_000).astype(np.int64)
+    fk = pxdata.random_column(g, 70_000, np.int64, -1000, 31_000)
+    L = px.load()
+    need = L.px_join_table_bytes(pk.size, 0)
+    buf = torch.empty(need + 64, dtype=torch.uint8, device="cuda")
+    pr, br, _ = oracle.join(pk, fk)
+    for off in (16, 32, 48):
+        table = buf[off:off + need]
+        ws = px.Workspace(1 << 20)
+        px.px_join_build([dev(pk)], 0, table=table, ws=ws)
+        res = px.px_join_probe(table, [dev(fk)], 0, probe_row=True, build_row=True, ws=ws)
+        assert ws.status() == px.PX_OK
+        m = count(res["nout"])
+        assert m == pr.size
+        np.testing.assert_array_equal(host(res["probe_row"], m), pr)
+        np.testing.assert_array_equal(host(res["build_row"], m), br)
+
+
 def test_join_multi_match_parity(px):
     g = pxdata.rng(302)
     pk = pxdata.random_column(g, 3000, np.int64, 0, 700)       # ~4 duplicates per key
