@@ -221,9 +221,13 @@ size_t px_join_build_ws_bytes(int64_t nbuild);
  * key value INT64_MIN is reserved as the empty-slot marker: a build key equal to
  * it records PX_ERR_UNSUPPORTED (probe keys equal to it never match). d_table
  * (table_bytes >= px_join_table_bytes) is caller memory with a private layout; it
- * stays valid for probes until rebuilt or freed. */
+ * stays valid for probes until rebuilt or freed. pay_col >= 0 (a PX_I8 or PX_I32
+ * column of `build`, not pk_col) is copied into the table beside each key: a probe
+ * whose build_payload is that one column (same address and type) reads the copy,
+ * i.e. the column's values at build time, in the same memory access as the key,
+ * instead of gathering them; pay_col = -1 copies nothing. */
 px_status px_join_build(const px_batch* build, int32_t pk_col,
-                        const int64_t* d_seg, int32_t nsegs, int32_t unique,
+                        const int64_t* d_seg, int32_t nsegs, int32_t unique, int32_t pay_col,
                         void* d_table, size_t table_bytes,
                         void* d_ws, size_t ws_bytes, void* stream);
 

@@ -106,7 +106,7 @@ def _declare(lib):
         "px_partition_tuned": ([BP, I32, P, P, I32, U64, BP, P, ctypes.POINTER(px_partition_config), P, SZ, P], I32),
         "px_join_table_bytes": ([I64, I32], SZ),
         "px_join_build_ws_bytes": ([I64], SZ),
-        "px_join_build": ([BP, I32, P, I32, I32, P, SZ, P, SZ, P], I32),
+        "px_join_build": ([BP, I32, P, I32, I32, I32, P, SZ, P, SZ, P], I32),
         "px_join_probe_ws_bytes": ([I64], SZ),
         "px_join_probe": ([P, BP, I32, P, P, P, I32, P, I32, BP, BP, P, P, P, P, P, SZ, P], I32),
         "px_groupby_ws_bytes": ([I64, I64], SZ),
@@ -292,9 +292,12 @@ def px_partition(cols, key_col: int, nparts: int, seed: int = 0, *, sel=None, ns
     return out, offsets
 
 
-def px_join_build(cols, pk_col: int, *, seg=None, unique: bool = True, d_nrows=None, table=None, ws=None,
-                  stream=None):
-    """Build a (per-segment) hash table on cols[pk_col] (join build pipeline). Returns the table tensor."""
+def px_join_build(cols, pk_col: int, *, seg=None, unique: bool = True, pay_col=None, d_nrows=None, table=None,
+                  ws=None, stream=None):
+    """Build a (per-segment) hash table on cols[pk_col] (join build pipeline). Returns the table tensor.
+
+    pay_col: a build column (int8 or int32) copied beside each key; probes whose payload
+    is exactly that column read the copy instead of gathering it."""
     L = load()
     n = cols[0].numel()
     nsegs = 0 if seg is None else seg.numel() - 1
@@ -303,8 +306,8 @@ def px_join_build(cols, pk_col: int, *, seg=None, unique: bool = True, d_nrows=N
         need, dtype=torch.uint8, device=cols[0].device)
     b = _Batch(cols, n, d_nrows)
     ws = _ws(ws, L.px_join_build_ws_bytes(n), stream)
-    _check(L.px_join_build(b.ref(), pk_col, _ptr(seg), nsegs, 1 if unique else 0, table.data_ptr(), table.numel(),
-                           ws.ptr, ws.nbytes, _stream(stream)), "px_join_build")
+    _check(L.px_join_build(b.ref(), pk_col, _ptr(seg), nsegs, 1 if unique else 0, -1 if pay_col is None else pay_col,
+                           table.data_ptr(), table.numel(), ws.ptr, ws.nbytes, _stream(stream)), "px_join_build")
     return table
 
 

@@ -103,15 +103,19 @@ __device__ __forceinline__ void add_split(uint32_t* lo, uint32_t* hi, uint64_t x
     if (add_hi) red_add_shared(hi, add_hi);
 }
 
-// Build row of `key` in an unsegmented unique table, or -1.
-__device__ __forceinline__ int32_t probe_row(const TableView& t, uint32_t nb, int64_t key) {
+// Build row of `key` (not kEmpty) in an unsegmented unique table, or -1; *pay
+// receives the payload value copied beside the key (meaningful when the table
+// holds one).
+__device__ __forceinline__ int32_t probe_row(const TableView& t, uint32_t nb, int64_t key, int32_t* pay) {
     const Bucket* bp = t.bk + home_bucket(static_cast<uint64_t>(key), nb);
     for (uint32_t round = 0; round < nb; ++round) {
-        const longlong2 k01 = *reinterpret_cast<const longlong2*>(&bp->key[0]);
-        const longlong2 k23 = *reinterpret_cast<const longlong2*>(&bp->key[2]);
+        const BucketRegs v = load_bucket(bp);
         bool end;
-        const int l = bucket_find(k01, k23, key, &end);
-        if (l >= 0) return bp->row[l];
+        const int l = bucket_find(v, key, &end);
+        if (l >= 0) {
+            *pay = bucket_pay(v, l);
+            return bucket_row(v, l);
+        }
         if (end) return -1;
         bp = bp + 1 == t.bk + nb ? t.bk : bp + 1;
     }
@@ -125,6 +129,8 @@ __device__ void frag_rows(const FragDev& f, int64_t r0, int64_t r1, uint32_t* s_
                           uint32_t* s_occ, int32_t* status) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t nb = static_cast<uint32_t>(table_buckets(f.t.hdr->nbuild, 1));
+    // the group column copied into the table at build time: read with the key
+    const bool group_in_table = f.t.hdr->pay_src == f.group && f.t.hdr->pay_w == f.group_w;
     const int naggs = f.naggs;
     for (int64_t tb = r0; tb < r1; tb += THREADS * ITEMS) {
         int64_t key[ITEMS], v[NA][ITEMS];
@@ -158,9 +164,11 @@ __device__ void frag_rows(const FragDev& f, int64_t r0, int64_t r1, uint32_t* s_
         for (int i = 0; i < ITEMS; ++i) {
             slot[i] = 0xffffffffu;
             if (!pass[i] || key[i] == kEmpty) continue;
-            const int32_t br = probe_row(f.t, nb, key[i]);
+            int32_t pay = 0;
+            const int32_t br = probe_row(f.t, nb, key[i], &pay);
             if (br < 0) continue;
-            const uint64_t d = static_cast<uint64_t>(load_w(f.group, f.group_w, br) - f.group_lo);
+            const int64_t gk = group_in_table ? static_cast<int64_t>(pay) : load_w(f.group, f.group_w, br);
+            const uint64_t d = static_cast<uint64_t>(gk - f.group_lo);
             if (d < f.D) slot[i] = static_cast<uint32_t>(d);
             else set_status(status, PX_ERR_UNSUPPORTED);
         }

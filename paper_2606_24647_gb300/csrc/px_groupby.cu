@@ -406,7 +406,11 @@ __device__ void aggregate_range_dense(const Spec& sp, const Smem& m, const int32
     uint32_t* const OCC = DIRECT ? nullptr : rep_occ(sp, m, rep);
     const uint64_t ebase = static_cast<uint64_t>(q) * sp.D;
     SegGeom geo = {};
-    if (PROBE) geo = seg_geom(sp.probe_t, q);
+    bool group_in_table = false;  // PROBE: the table holds the group column beside the keys
+    if (PROBE) {
+        geo = seg_geom(sp.probe_t, q);
+        group_in_table = sp.probe_t.hdr->pay_src == sp.group_col && sp.probe_t.hdr->pay_w == sp.group_w;
+    }
     for (int64_t tb = a0; tb < a1; tb += kTile) {
         int32_t row[kItems];
         uint32_t idx[kItems];
@@ -417,42 +421,40 @@ __device__ void aggregate_range_dense(const Spec& sp, const Smem& m, const int32
             row[i] = j < a1 ? (sel ? sel[j] : static_cast<int32_t>(j)) : -1;
         }
         if (PROBE) {
-            // Join probe of every position: its key's home bucket (one sector), a walk
-            // on in the rare case that bucket is full without it, the build row, then
-            // the group key gathered from the build column.
+            // Join probe of every position: its key's home bucket (one sector: keys,
+            // rows and copied payload values), a walk on in the rare case that bucket
+            // is full without it, then the group key: the copied payload value when the
+            // table holds the group column, else gathered from the build column.
             int64_t fkv[kItems];
-            const Bucket* bp[kItems];
-            longlong2 k01[kItems], k23[kItems];
+            BucketRegs bv[kItems];
 #pragma unroll
             for (int i = 0; i < kItems; ++i) fkv[i] = row[i] >= 0 ? sp.probe_fk[row[i]] : kEmpty;
+            const Bucket* const segb = sp.probe_t.bk + geo.b0;
+            uint32_t hb[kItems];
 #pragma unroll
             for (int i = 0; i < kItems; ++i) {
-                bp[i] = sp.probe_t.bk + geo.b0 + home_bucket(static_cast<uint64_t>(fkv[i]), geo.nb);
-                if (fkv[i] != kEmpty) {
-                    k01[i] = *reinterpret_cast<const longlong2*>(&bp[i]->key[0]);
-                    k23[i] = *reinterpret_cast<const longlong2*>(&bp[i]->key[2]);
-                } else {
-                    k01[i] = k23[i] = make_longlong2(kEmpty, kEmpty);
-                }
+                hb[i] = home_bucket(static_cast<uint64_t>(fkv[i]), geo.nb);
+                bv[i] = load_bucket(segb + hb[i]);  // hb < nb: inside the segment
             }
-            int32_t brow[kItems];
+            int32_t brow[kItems], bpay[kItems];
 #pragma unroll
             for (int i = 0; i < kItems; ++i) {
                 brow[i] = -1;
+                bpay[i] = 0;
                 if (fkv[i] == kEmpty) continue;
                 bool end;
-                int l = bucket_find(k01[i], k23[i], fkv[i], &end);
-                const Bucket* b = bp[i];
-                for (uint32_t round = 1; l < 0 && !end && round < geo.nb; ++round) {
-                    b = b + 1 == sp.probe_t.bk + geo.b0 + geo.nb ? sp.probe_t.bk + geo.b0 : b + 1;
-                    l = bucket_find(*reinterpret_cast<const longlong2*>(&b->key[0]),
-                                    *reinterpret_cast<const longlong2*>(&b->key[2]), fkv[i], &end);
+                int l = bucket_find(bv[i], fkv[i], &end);
+                if (l < 0 && !end) l = walk_find(segb, geo.nb, hb[i], fkv[i], &bv[i]);
+                if (l >= 0) {
+                    brow[i] = bucket_row(bv[i], l);
+                    bpay[i] = bucket_pay(bv[i], l);
                 }
-                if (l >= 0) brow[i] = b->row[l];
             }
 #pragma unroll
             for (int i = 0; i < kItems; ++i) {
-                pkey[i] = brow[i] >= 0 ? load_int(sp.group_col, sp.group_w, brow[i]) : 0;
+                pkey[i] = brow[i] < 0 ? 0
+                                      : (group_in_table ? static_cast<int64_t>(bpay[i])
+                                                           : load_int(sp.group_col, sp.group_w, brow[i]));
                 const uint64_t o0 = static_cast<uint64_t>(pkey[i] - sp.lo[0]);
                 idx[i] = brow[i] < 0 ? kIdxNone : (o0 < sp.span[0] ? static_cast<uint32_t>(o0) : kIdxOutside);
             }

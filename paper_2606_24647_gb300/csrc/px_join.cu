@@ -2,20 +2,14 @@
 // the join-heavy queries Q5/Q9 of Sec. 3.4), per partition after the exchange
 // when segments are given.
 //
-// Table (caller memory, private layout):
-//   [0, 64)            header: magic, nsegs, unique flag
-//   [64, 64 + A)       copy of the build segment offsets (nsegs + 1 int64)
-//   [64 + A, ...)      buckets of 64 bytes: 4 int64 keys, their 4 int32 build
-//                      rows, 16 bytes of padding
-// Segment q of n_q rows owns buckets [b_q, b_{q+1}) with b_q = floor(seg[q] / 2) + q,
-// i.e. at least (n_q + 1) / 2 buckets = 2 n_q + 2 slots, so every segment runs at
-// load factor < 1/2 and the whole table is floor(n / 2) + nsegs buckets with no
-// size known before the build. Slots are numbered 4 * bucket + lane. Linear
-// probing over slots starts at the first slot of the key's home bucket: the
-// multiply-shift reduction of the LOWER 32 bits of fmix64(key) (the exchange uses
-// the upper 32) onto the segment's buckets. The 4 keys of a bucket share one
-// aligned 32-byte sector, so the first 4 probes cost one sector read. Empty slots
-// hold the key INT64_MIN.
+// Table: caller memory with the private layout of px_table.cuh (32-byte buckets
+// of 2 slots: keys, build rows, payload values; segment q owns n_q + 1 buckets, so
+// every segment runs at load factor < 1/2 and the whole table is n + nsegs buckets
+// with no size known before the build). Linear probing over slots starts at the
+// first slot of the key's home bucket: the multiply-shift reduction of the LOWER
+// 32 bits of fmix64(key) (the exchange uses the upper 32) onto the segment's
+// buckets. A lookup reads its home bucket's whole sector (keys, rows and payload
+// values); empty slots hold the key INT64_MIN.
 #include <algorithm>
 
 #include "px_common.cuh"
@@ -27,7 +21,7 @@ namespace {
 // ------------------------------------------------------------------ build ----
 
 __global__ void build_init_kernel(TableView t, int32_t S, int32_t unique, const int64_t* __restrict__ d_seg,
-                                  const int64_t* __restrict__ d_n, int64_t ncap) {
+                                  const int64_t* __restrict__ d_n, int64_t ncap, const void* pay, int32_t pay_w) {
     const int64_t n = actual_rows(d_n, ncap);
     const int64_t gtid = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
     const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
@@ -36,6 +30,8 @@ __global__ void build_init_kernel(TableView t, int32_t S, int32_t unique, const 
         t.hdr->nsegs = S;
         t.hdr->unique = unique;
         t.hdr->nbuild = n;
+        t.hdr->pay_src = pay;
+        t.hdr->pay_w = pay ? pay_w : 0;
         // Segment offsets clamped to be non-decreasing within [0, n] and to end at
         // n, so no segment can address a bucket outside the table.
         int64_t prev = 0;
@@ -48,14 +44,16 @@ __global__ void build_init_kernel(TableView t, int32_t S, int32_t unique, const 
         }
         t.seg[S] = n;
     }
-    // Keys of every bucket to empty (16-byte stores; rows are written on insert).
-    const int64_t nwords = 2 * table_buckets(n, S);
-    for (int64_t w = gtid; w < nwords; w += stride)
-        reinterpret_cast<longlong2*>(&t.bk[w >> 1].key[2 * (w & 1)])[0] = make_longlong2(kEmpty, kEmpty);
+    // Keys of every bucket to empty (one 16-byte store per bucket; rows and payload
+    // values are written on insert).
+    const int64_t nbk = table_buckets(n, S);
+    for (int64_t w = gtid; w < nbk; w += stride)
+        *reinterpret_cast<longlong2*>(&t.bk[w].key[0]) = make_longlong2(kEmpty, kEmpty);
 }
 
 __global__ void build_insert_kernel(TableView t, int32_t S, int32_t unique, const int64_t* __restrict__ pk,
-                                    const int64_t* __restrict__ d_n, int64_t ncap, int32_t* status) {
+                                    const int64_t* __restrict__ d_n, int64_t ncap, const void* __restrict__ pay,
+                                    int32_t pay_w, int32_t* status) {
     const int64_t n = actual_rows(d_n, ncap);
     const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -67,15 +65,16 @@ __global__ void build_insert_kernel(TableView t, int32_t S, int32_t unique, cons
     const int q = S > 1 ? seg_of(t.seg, S, i) : 0;
     const SegGeom g = seg_geom(t, q);
     Bucket* bk = t.bk + g.b0;
-    const uint64_t nslots = 4ull * g.nb;
-    uint64_t s = 4ull * home_bucket(static_cast<uint64_t>(key), g.nb);
+    const uint64_t nslots = uint64_t(kSlots) * g.nb;
+    uint64_t s = uint64_t(kSlots) * home_bucket(static_cast<uint64_t>(key), g.nb);
     for (uint64_t probe = 0; probe < nslots; ++probe) {
-        Bucket& b = bk[s >> 2];
-        const unsigned long long prev = atomicCAS(reinterpret_cast<unsigned long long*>(&b.key[s & 3]),
+        Bucket& b = bk[s / kSlots];
+        const unsigned long long prev = atomicCAS(reinterpret_cast<unsigned long long*>(&b.key[s % kSlots]),
                                                   static_cast<unsigned long long>(kEmpty),
                                                   static_cast<unsigned long long>(key));
         if (prev == static_cast<unsigned long long>(kEmpty)) {
-            b.row[s & 3] = static_cast<int32_t>(i);
+            b.row[s % kSlots] = static_cast<int32_t>(i);
+            if (pay) b.pay[s % kSlots] = static_cast<int32_t>(load_int(pay, pay_w, i));
             return;
         }
         if (unique && prev == static_cast<unsigned long long>(key)) {
@@ -156,10 +155,10 @@ __device__ __forceinline__ void emit(const OutCols& oc, int64_t pos, int64_t pro
 // hold fewer than 2^30 rows, so segment slot numbers fit 32 bits.
 __device__ __forceinline__ int32_t count_matches(const Bucket* segb, uint32_t nb, uint32_t s, int64_t key,
                                                  uint32_t* first) {
-    const uint32_t nslots = 4 * nb;
+    const uint32_t nslots = kSlots * nb;
     int32_t m = 0;
     for (uint32_t probe = 0; probe < nslots; ++probe) {
-        const int64_t k = segb[s >> 2].key[s & 3];
+        const int64_t k = segb[s / kSlots].key[s % kSlots];
         if (k == key) {
             if (m == 0) *first = s;
             ++m;
@@ -221,29 +220,9 @@ __device__ __forceinline__ void cursor_seek(SegCursor& c, const TableView& t, co
 // through the following buckets: the key's build row, or kNoMatch at the first
 // empty slot. Occupied slots form a prefix of every probe sequence.
 __device__ __forceinline__ int32_t walk_on(const Bucket* segb, uint32_t nb, uint32_t hb, int64_t key) {
-    const Bucket* b = segb + hb;
-    for (uint32_t round = 1; round < nb; ++round) {
-        b = b + 1 == segb + nb ? segb : b + 1;
-        const longlong2 k01 = *reinterpret_cast<const longlong2*>(&b->key[0]);
-        const longlong2 k23 = *reinterpret_cast<const longlong2*>(&b->key[2]);
-        bool end;
-        const int l = bucket_find(k01, k23, key, &end);
-        if (l >= 0) return b->row[l];
-        if (end) break;
-    }
-    return kNoMatch;
-}
-
-// Unique table, one home bucket: the build row of `key` among the bucket's keys
-// k01, k23 and rows rv, else kNoMatch. A unique table holds a key at most once,
-// so the four compares select without ordering.
-__device__ __forceinline__ int32_t unique_pick(longlong2 k01, longlong2 k23, int4 rv, int64_t key) {
-    int32_t r = kNoMatch;
-    r = k01.x == key ? rv.x : r;
-    r = k01.y == key ? rv.y : r;
-    r = k23.x == key ? rv.z : r;
-    r = k23.y == key ? rv.w : r;
-    return r;
+    BucketRegs v;
+    const int l = walk_find(segb, nb, hb, key, &v);
+    return l >= 0 ? bucket_row(v, l) : kNoMatch;
 }
 
 // Persistent over tiles (grid-stride), software-pipelined: the next tile's keys
@@ -309,18 +288,11 @@ probe_match_kernel(TableView t, int32_t S, const int64_t* __restrict__ fk, const
         int32_t out[kMatchItems];
         int32_t cnt = 0;
         if (unique) {
-            // Every bucket is read whole (keys and rows): hb < nb keeps the reads
-            // inside the segment even for positions without a key.
-            longlong2 k01[kMatchItems], k23[kMatchItems];
-            int4 rv[kMatchItems];
+            // Every home bucket is read whole (one sector: keys and rows); hb < nb
+            // keeps the reads inside the segment even for positions without a key.
+            BucketRegs bv[kMatchItems];
 #pragma unroll
-            for (int i = 0; i < kMatchItems; ++i) {
-                const Bucket* b = segb[i] + hb[i];
-                const longlong4_32a k = *reinterpret_cast<const longlong4_32a*>(&b->key[0]);  // one 32-byte load
-                k01[i] = make_longlong2(k.x, k.y);
-                k23[i] = make_longlong2(k.z, k.w);
-                rv[i] = *reinterpret_cast<const int4*>(&b->row[0]);
-            }
+            for (int i = 0; i < kMatchItems; ++i) bv[i] = load_bucket(segb[i] + hb[i]);
             // Next tile's keys go out while this tile's buckets are in flight.
             int64_t keyn[kMatchItems];
             match_keys<kSel>(fk, sel, nv, (tile + gridDim.x) * kTile + lane_off, keyn);
@@ -328,9 +300,11 @@ probe_match_kernel(TableView t, int32_t S, const int64_t* __restrict__ fk, const
 #pragma unroll
             for (int i = 0; i < kMatchItems; ++i) {
                 const bool live = keyv[i] != kEmpty;  // a row, and not the reserved key
-                const int32_t r = unique_pick(k01[i], k23[i], rv[i], keyv[i]);
+                // a unique table holds a key at most once: the compares select unordered
+                int32_t r = bv[i].k0 == keyv[i] ? bv[i].r0 : kNoMatch;
+                r = bv[i].k1 == keyv[i] ? bv[i].r1 : r;
                 out[i] = live ? r : kNoMatch;
-                if (live && r < 0 && k23[i].y != kEmpty) pend |= 1u << i;
+                if (live && r < 0 && bv[i].k1 != kEmpty) pend |= 1u << i;
             }
             if (__any_sync(FULL, pend != 0)) {
 #pragma unroll
@@ -350,10 +324,10 @@ probe_match_kernel(TableView t, int32_t S, const int64_t* __restrict__ fk, const
                 out[i] = kNoMatch;
                 if (keyv[i] == kEmpty) continue;
                 uint32_t first = 0;
-                const int32_t m = count_matches(segb[i], nb[i], 4 * hb[i], keyv[i], &first);
+                const int32_t m = count_matches(segb[i], nb[i], kSlots * hb[i], keyv[i], &first);
                 const int64_t b0 = segb[i] - t.bk;
-                if (m == 1) out[i] = segb[i][first >> 2].row[first & 3];
-                else if (m > 1) out[i] = -static_cast<int32_t>(4 * b0 + first) - 2;
+                if (m == 1) out[i] = segb[i][first / kSlots].row[first % kSlots];
+                else if (m > 1) out[i] = -static_cast<int32_t>(kSlots * b0 + first) - 2;
                 cnt += m;
             }
             match_keys<kSel>(fk, sel, nv, (tile + gridDim.x) * kTile + lane_off, keyv);
@@ -496,7 +470,7 @@ probe_emit_kernel(TableView t, int32_t S, const int64_t* __restrict__ fk, const 
                 key[i] = 0;
                 if (mr[i] < kNoMatch) {
                     const SegGeom g = seg_geom(t, S > 1 ? seg_of(pseg, S, tb + lp[i]) : 0);
-                    const uint32_t first = static_cast<uint32_t>(-static_cast<int64_t>(mr[i]) - 2 - 4 * g.b0);
+                    const uint32_t first = static_cast<uint32_t>(-static_cast<int64_t>(mr[i]) - 2 - kSlots * g.b0);
                     key[i] = fk[prow[i]];
                     uint32_t dummy = 0;
                     m[i] = count_matches(t.bk + g.b0, g.nb, first, key[i], &dummy);
@@ -550,13 +524,13 @@ probe_emit_kernel(TableView t, int32_t S, const int64_t* __restrict__ fk, const 
         if (mr[i] >= kNoMatch) continue;
         const SegGeom g = seg_geom(t, S > 1 ? seg_of(pseg, S, tb + lp[i]) : 0);
         const Bucket* segb = t.bk + g.b0;
-        const uint32_t nslots = 4 * g.nb;
-        uint32_t s = static_cast<uint32_t>(-static_cast<int64_t>(mr[i]) - 2 - 4 * g.b0);
+        const uint32_t nslots = kSlots * g.nb;
+        uint32_t s = static_cast<uint32_t>(-static_cast<int64_t>(mr[i]) - 2 - kSlots * g.b0);
         int64_t p = pos[i];
         for (uint32_t probe = 0; probe < nslots && p < pos[i] + m[i]; ++probe) {
-            const int64_t k = segb[s >> 2].key[s & 3];
+            const int64_t k = segb[s / kSlots].key[s % kSlots];
             if (k == key[i]) {
-                if (p < out_cap) emit(oc, p, prow[i], segb[s >> 2].row[s & 3], probe_row, build_row);
+                if (p < out_cap) emit(oc, p, prow[i], segb[s / kSlots].row[s % kSlots], probe_row, build_row);
                 ++p;
             } else if (k == kEmpty) {
                 break;
@@ -594,7 +568,7 @@ probe_seg_kernel(TableView t, int32_t S, int32_t segmented, const int64_t* __res
             cnt = 1;
         } else if (r < kNoMatch) {  // first of several matches: count them along the chain
             const SegGeom g = seg_geom(t, S > 1 ? seg_of(pseg, S, j) : 0);
-            const uint32_t first = static_cast<uint32_t>(-static_cast<int64_t>(r) - 2 - 4 * g.b0);
+            const uint32_t first = static_cast<uint32_t>(-static_cast<int64_t>(r) - 2 - kSlots * g.b0);
             uint32_t dummy = 0;
             cnt = count_matches(t.bk + g.b0, g.nb, first, fk[sel ? static_cast<int64_t>(sel[j]) : j], &dummy);
         }
@@ -638,7 +612,7 @@ extern "C" {
 size_t px_join_table_bytes(int64_t nbuild, int32_t nsegs) {
     if (nbuild < 0) nbuild = 0;
     const int32_t S = nsegs > 0 ? nsegs : 1;
-    return 64 + seg_area_bytes(S) + 48 + static_cast<size_t>(table_buckets(nbuild, S)) * sizeof(Bucket);
+    return 64 + seg_area_bytes(S) + 16 + static_cast<size_t>(table_buckets(nbuild, S)) * sizeof(Bucket);
 }
 
 size_t px_join_build_ws_bytes(int64_t nbuild) {
@@ -651,13 +625,20 @@ size_t px_join_probe_ws_bytes(int64_t nprobe) {
 }
 
 px_status px_join_build(const px_batch* build, int32_t pk_col, const int64_t* d_seg, int32_t nsegs, int32_t unique,
-                        void* d_table, size_t table_bytes, void* d_ws, size_t ws_bytes, void* stream) {
+                        int32_t pay_col, void* d_table, size_t table_bytes, void* d_ws, size_t ws_bytes,
+                        void* stream) {
     CallRange nvtx_range("px_join_build");
     set_error("");
     px_status s = check_batch(build, "px_join_build build");
     if (s != PX_OK) return s;
     if (pk_col < 0 || pk_col >= build->ncols) return fail(PX_ERR_INVALID, "px_join_build: pk_col %d", pk_col);
     if (build->cols[pk_col].type != PX_I64) return fail(PX_ERR_INVALID, "px_join_build: key column must be PX_I64");
+    if (pay_col < -1 || pay_col >= build->ncols || pay_col == pk_col)
+        return fail(PX_ERR_INVALID, "px_join_build: pay_col %d", pay_col);
+    if (pay_col >= 0 && build->cols[pay_col].type != PX_I8 && build->cols[pay_col].type != PX_I32)
+        return fail(PX_ERR_UNSUPPORTED, "px_join_build: the copied payload column must be PX_I8 or PX_I32");
+    const void* pay = pay_col >= 0 ? build->cols[pay_col].data : nullptr;
+    const int32_t pay_w = pay_col >= 0 ? build->cols[pay_col].type : 0;
     if (nsegs < 0 || nsegs > PX_MAX_SEGS)
         return fail(PX_ERR_UNSUPPORTED, "px_join_build: nsegs %d outside [0, %d]", nsegs, PX_MAX_SEGS);
     if ((nsegs > 0) != (d_seg != nullptr))
@@ -666,7 +647,7 @@ px_status px_join_build(const px_batch* build, int32_t pk_col, const int64_t* d_
     if (table_bytes < px_join_table_bytes(build->nrows, nsegs))
         return fail(PX_ERR_INVALID, "px_join_build: table of %zu bytes, %zu needed", table_bytes,
                     px_join_table_bytes(build->nrows, nsegs));
-    if (!unique && 4 * table_buckets(build->nrows, nsegs > 0 ? nsegs : 1) + 2 > INT32_MAX)
+    if (!unique && kSlots * table_buckets(build->nrows, nsegs > 0 ? nsegs : 1) + 2 > INT32_MAX)
         return fail(PX_ERR_UNSUPPORTED, "px_join_build: multi-map tables hold below about 2^30 rows");
     s = check_ws(d_ws, ws_bytes, px_join_build_ws_bytes(build->nrows), "px_join_build");
     if (s != PX_OK) return s;
@@ -674,16 +655,16 @@ px_status px_join_build(const px_batch* build, int32_t pk_col, const int64_t* d_
     const int32_t S = nsegs > 0 ? nsegs : 1;
     const TableView t = table_view(d_table, S);
     const int64_t ncap = build->nrows;
-    const int64_t nwords = 2 * table_buckets(ncap, S);  // 16-byte key words to clear
+    const int64_t nwords = table_buckets(ncap, S);  // buckets whose keys to clear
     const int threads = 256;
     const unsigned init_blocks = static_cast<unsigned>(std::min<int64_t>(cdiv(nwords, threads), 8192));
-    build_init_kernel<<<init_blocks, threads, 0, st>>>(t, S, unique ? 1 : 0, d_seg, build->d_nrows, ncap);
+    build_init_kernel<<<init_blocks, threads, 0, st>>>(t, S, unique ? 1 : 0, d_seg, build->d_nrows, ncap, pay, pay_w);
     note_launch();
     if ((s = check_launch("px_join_build init")) != PX_OK) return s;
     if (ncap > 0) {
         build_insert_kernel<<<static_cast<unsigned>(cdiv(ncap, threads)), threads, 0, st>>>(
-            t, S, unique ? 1 : 0, static_cast<const int64_t*>(build->cols[pk_col].data), build->d_nrows, ncap,
-            &static_cast<WsHeader*>(d_ws)->status);
+            t, S, unique ? 1 : 0, static_cast<const int64_t*>(build->cols[pk_col].data), build->d_nrows, ncap, pay,
+            pay_w, &static_cast<WsHeader*>(d_ws)->status);
         note_launch();
         if ((s = check_launch("px_join_build insert")) != PX_OK) return s;
     }
@@ -780,8 +761,8 @@ px_status px_join_probe(const void* d_table, const px_batch* probe, int32_t fk_c
     note_launch();
     if ((s = check_launch("px_join_probe emit")) != PX_OK) return s;
     if (d_out_seg) {
-        probe_seg_kernel<<<static_cast<unsigned>(S + 1), kTile, 0, st>>>(t, S, nsegs > 0 ? 1 : 0, d_seg, fk, d_sel, d_n, ncap, mrow, toff,
-                                                     d_nout, d_out_seg);
+        probe_seg_kernel<<<static_cast<unsigned>(S + 1), kTile, 0, st>>>(t, S, nsegs > 0 ? 1 : 0, d_seg, fk, d_sel,
+                                                                          d_n, ncap, mrow, toff, d_nout, d_out_seg);
         note_launch();
         if ((s = check_launch("px_join_probe segments")) != PX_OK) return s;
     }

@@ -127,7 +127,7 @@ class JoinPipeline:
         return list(zip(self.CALLS, [
             lambda: px_filter(self.d["date"], self.lo, self.hi, sel=self.sel, nsel=self.nsel, ws=self.ws,
                               stream=stream),
-            lambda: px_join_build(self.dim, 0, unique=True, table=self.table, ws=self.ws, stream=stream),
+            lambda: px_join_build(self.dim, 0, unique=True, pay_col=1, table=self.table, ws=self.ws, stream=stream),
             probe, groupby]))
 
     def run(self, stream=None) -> dict:
@@ -193,7 +193,8 @@ class AtScalePipeline:
         px_partition(self.fact, 0, P, self.seed, out=self.fparts, offsets=self.foff, config=self.fact_config, ws=ws,
                      stream=stream)
         mark(2)
-        px_join_build(self.dparts, 0, seg=self.doff, unique=True, table=self.table, ws=ws, stream=stream)
+        px_join_build(self.dparts, 0, seg=self.doff, unique=True, pay_col=1, table=self.table, ws=ws,
+                      stream=stream)
         mark(3)
         j = px_join_probe(self.table, self.fparts, 0, seg=self.foff, carry=[1], payload=[self.dparts[1]],
                           out=self.jout, out_cap=self.jout[0].numel(), out_seg=True, ws=ws, stream=stream)
@@ -220,7 +221,8 @@ class AtScalePipeline:
         px_partition(self.fact, 0, P, self.seed, out=self.fparts, offsets=self.foff, config=self.fact_config, ws=ws,
                      stream=stream)
         mark(2)
-        px_join_build(self.dparts, 0, seg=self.doff, unique=True, table=self.table, ws=ws, stream=stream)
+        px_join_build(self.dparts, 0, seg=self.doff, unique=True, pay_col=1, table=self.table, ws=ws,
+                      stream=stream)
         mark(3)
         part = px_join_probe_agg(self.table, self.fparts, 0, self.dparts[1], (lo, hi),
                                  [(PX_SUM, 1, None), (PX_COUNT, None, None)], max_groups=self.max_partial,
@@ -250,7 +252,8 @@ class FragmentSet:
         for d, ng in zip(datas, self.ngroups):
             c = {k: torch.from_numpy(d[k]).to(dev, non_blocking=True) for k in ("key", "price", "qty", "date", "pk", "attr")}
             c["table"] = torch.empty(L.px_join_table_bytes(max(1, d["pk"].size), 0), dtype=torch.uint8, device=dev)
-            px_join_build([c["pk"], c["attr"]], 0, unique=True, table=c["table"], ws=ws, stream=stream)
+            px_join_build([c["pk"], c["attr"]], 0, unique=True, pay_col=1, table=c["table"], ws=ws,
+                          stream=stream)
             self.cols.append(c)
             self.frags.append({"key": c["key"], "filter": c["date"], "lo": lo, "hi": hi,
                                "cols": [c["price"], c["qty"]],
@@ -361,7 +364,8 @@ class WideJoinPipeline:
         px_partition(self.fact, 0, P, self.seed, out=self.fparts, offsets=self.foff, ws=ws, stream=stream)
         k += 1
         mark(k)
-        px_join_build(self.dparts, 0, seg=self.doff, unique=True, table=self.table, ws=ws, stream=stream)
+        px_join_build(self.dparts, 0, seg=self.doff, unique=True, pay_col=1, table=self.table, ws=ws,
+                      stream=stream)
         k += 1
         mark(k)
         carry = [1] if self.late else [1, 2, 3]

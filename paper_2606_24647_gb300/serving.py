@@ -76,7 +76,7 @@ class ResidentDim:
         L = load()
         self.pk, self.attr, self.ngroups = pk, attr, int(ngroups)
         self.table = torch.empty(L.px_join_table_bytes(max(1, pk.numel()), 0), dtype=torch.uint8, device=pk.device)
-        px_join_build([pk, attr], 0, unique=True, table=self.table, ws=ws)
+        px_join_build([pk, attr], 0, unique=True, pay_col=1, table=self.table, ws=ws)
 
 
 class Query:

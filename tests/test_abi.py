@@ -108,8 +108,8 @@ def test_host_checks(lib):
     assert r == pxm.PX_ERR_INVALID
     # join build: table too small, segments without offsets
     b = _batch(pxm, [pxm.PX_I64], 100)
-    assert lib.px_join_build(ctypes.byref(b), 0, None, 0, 1, FAKE, 64, ws, wsz, None) == pxm.PX_ERR_INVALID
-    assert lib.px_join_build(ctypes.byref(b), 0, None, 4, 1, FAKE, 1 << 30, ws, wsz, None) == pxm.PX_ERR_INVALID
+    assert lib.px_join_build(ctypes.byref(b), 0, None, 0, 1, -1, FAKE, 64, ws, wsz, None) == pxm.PX_ERR_INVALID
+    assert lib.px_join_build(ctypes.byref(b), 0, None, 4, 1, -1, FAKE, 1 << 30, ws, wsz, None) == pxm.PX_ERR_INVALID
     # group-by: too many key bits with segments, wrong output arity
     g_in = _batch(pxm, [pxm.PX_I64, pxm.PX_I64], 100)
     g_out = _batch(pxm, [pxm.PX_I64, pxm.PX_I64], 100)
@@ -269,14 +269,18 @@ def test_host_checks_of_join_build_and_gather(lib):
     import paper_2606_24647_gb300 as pxm
     ws, wsz = FAKE, 1 << 30
     I32, I64 = pxm.PX_I32, pxm.PX_I64
-    b = _batch(pxm, [I64, I32], 100)
+    b = _batch(pxm, [I64, I32, I64], 100)
     big = lib.px_join_table_bytes(100, 0)
 
-    def build(bb=b, pk=0, seg=None, nsegs=0, unique=1, table=FAKE, tbytes=1 << 30, wsb=wsz):
-        return lib.px_join_build(ctypes.byref(bb), pk, seg, nsegs, unique, table, tbytes, ws, wsb, None)
+    def build(bb=b, pk=0, seg=None, nsegs=0, unique=1, pay=-1, table=FAKE, tbytes=1 << 30, wsb=wsz):
+        return lib.px_join_build(ctypes.byref(bb), pk, seg, nsegs, unique, pay, table, tbytes, ws, wsb, None)
 
     cases = [
-        (dict(pk=2), pxm.PX_ERR_INVALID, "pk_col"),
+        (dict(pk=3), pxm.PX_ERR_INVALID, "pk_col"),
+        (dict(pay=3), pxm.PX_ERR_INVALID, "pay_col"),
+        (dict(pay=0), pxm.PX_ERR_INVALID, "pay_col"),
+        (dict(pay=-2), pxm.PX_ERR_INVALID, "pay_col"),
+        (dict(pay=2), pxm.PX_ERR_UNSUPPORTED, "PX_I8 or PX_I32"),
         (dict(pk=1), pxm.PX_ERR_INVALID, "PX_I64"),
         (dict(nsegs=4097, seg=FAKE), pxm.PX_ERR_UNSUPPORTED, "nsegs"),
         (dict(nsegs=3), pxm.PX_ERR_INVALID, "d_seg"),

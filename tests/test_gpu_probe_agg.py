@@ -32,8 +32,9 @@ def test_probe_agg_segmented_partial_matches_oracle(px):
     assert n == count(r["final"]["ngroups"])
 
 
+@pytest.mark.parametrize("in_table", [False, True])
 @pytest.mark.parametrize("rng", ["exact", "narrow"])
-def test_probe_agg_single_with_selection_and_misses(px, rng):
+def test_probe_agg_single_with_selection_and_misses(px, rng, in_table):
     d = pxdata.plain_join(20_000, 300_003, nattr=25)
     g = pxdata.rng(900)
     d["fk"][::11] = g.integers(20_001, 30_000, size=d["fk"][::11].size)  # keys with no match
@@ -41,7 +42,8 @@ def test_probe_agg_single_with_selection_and_misses(px, rng):
     pr, br, _ = oracle.join(d["pk"], d["fk"], sel=sel)
     want = oracle.groupby([d["attr"][br]], [(oracle.SUM, d["amount"][pr], None), (oracle.COUNT, None, None)])
     dim = [dev(d["pk"]), dev(d["attr"])]
-    table = px.px_join_build(dim, 0, unique=True)
+    # in_table: the group column is copied beside the keys and read from the table
+    table = px.px_join_build(dim, 0, unique=True, pay_col=1 if in_table else None)
     lo, hi = (0, 24) if rng == "exact" else (5, 12)  # narrow: keys outside take the hash path
     res = px.px_join_probe_agg(table, [dev(d["fk"]), dev(d["amount"])], 0, dim[1], (lo, hi),
                                [(px.PX_SUM, 1, None), (px.PX_COUNT, None, None)], max_groups=64,
