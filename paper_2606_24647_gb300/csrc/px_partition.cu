@@ -36,6 +36,10 @@ constexpr int kOffRegs = (PX_MAX_PARTS + kThreads - 1) / kThreads;  // partition
 constexpr int kScanThreads = 256;
 constexpr int kScanItems = 32;  // 8192 counts per scan tile: a short look-back chain
 constexpr int kScanTile = kScanThreads * kScanItems;
+// Up to this many partitions the histogram pass stores each position's partition id
+// (one byte) for the scatter, which then stages the ids instead of hashing the keys
+// again: one byte written and read per row against a hash per row.
+constexpr int32_t kPidMaxParts = 256;
 
 struct Cols {
     int32_t ncols;
@@ -64,7 +68,7 @@ template <int ITEMS>
 __global__ void __launch_bounds__(kThreads)
 part_hist_kernel(const int64_t* __restrict__ key, const int32_t* __restrict__ sel,
                  const int64_t* __restrict__ d_nsel, int64_t ncap, uint64_t seed, uint32_t nparts,
-                 int32_t* __restrict__ cnt, int64_t ntiles) {
+                 int32_t* __restrict__ cnt, int64_t ntiles, uint8_t* __restrict__ pid_out) {
     constexpr int T = kThreads * ITEMS;
     extern __shared__ int32_t s_hist[];  // [kWarps][nparts]
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -72,11 +76,35 @@ part_hist_kernel(const int64_t* __restrict__ key, const int32_t* __restrict__ se
     const int64_t n = actual_rows(d_nsel, ncap);
     const int64_t tbase = static_cast<int64_t>(blockIdx.x) * T;
     uint32_t p[ITEMS];
+    if (!sel && tbase + T <= n && (reinterpret_cast<uintptr_t>(key) & 15) == 0) {
+        // A full tile of a plain column: only counts matter here, so each thread
+        // takes ITEMS consecutive keys with 16-byte loads.
+        const longlong2* kv = reinterpret_cast<const longlong2*>(key + tbase + static_cast<int64_t>(tid) * ITEMS);
 #pragma unroll
-    for (int i = 0; i < ITEMS; ++i) {
-        const int64_t j = tbase + local_pos<ITEMS>(warp, i, lane);
-        p[i] = nparts;
-        if (j < n) p[i] = part_of(key[sel ? static_cast<int64_t>(sel[j]) : j], seed, nparts);
+        for (int i = 0; i < ITEMS / 2; ++i) {
+            const longlong2 k2 = kv[i];
+            p[2 * i] = part_of(k2.x, seed, nparts);
+            p[2 * i + 1] = part_of(k2.y, seed, nparts);
+        }
+        if (pid_out) {  // the ids of this thread's ITEMS consecutive positions, one store
+            uint64_t w = 0;
+#pragma unroll
+            for (int i = 0; i < ITEMS; ++i) w |= static_cast<uint64_t>(p[i]) << (8 * i);
+            uint8_t* o = pid_out + tbase + static_cast<int64_t>(tid) * ITEMS;
+            if (ITEMS == 8) *reinterpret_cast<uint64_t*>(o) = w;
+            else if (ITEMS == 4) *reinterpret_cast<uint32_t*>(o) = static_cast<uint32_t>(w);
+            else *reinterpret_cast<uint16_t*>(o) = static_cast<uint16_t>(w);
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < ITEMS; ++i) {
+            const int64_t j = tbase + local_pos<ITEMS>(warp, i, lane);
+            p[i] = nparts;
+            if (j < n) {
+                p[i] = part_of(key[sel ? static_cast<int64_t>(sel[j]) : j], seed, nparts);
+                if (pid_out) pid_out[j] = static_cast<uint8_t>(p[i]);
+            }
+        }
     }
     __syncthreads();
     int32_t* wh = s_hist + warp * nparts;
@@ -216,7 +244,7 @@ __global__ void __launch_bounds__(kThreads, ITEMS >= 8 ? 3 : 4)
 part_scatter_kernel(Cols cols, int32_t key_col, const int32_t* __restrict__ sel,
                     const int64_t* __restrict__ d_nsel, int64_t ncap, uint64_t seed, uint32_t nparts,
                     const int32_t* __restrict__ offs, int64_t ntiles, uint32_t stage_bytes, uint32_t row_bytes,
-                    int32_t* status) {
+                    const uint8_t* __restrict__ pid_in, int32_t* status) {
     constexpr int T = kThreads * ITEMS;
     extern __shared__ __align__(16) unsigned char smem[];
     const int np1 = static_cast<int>(nparts) + 1;
@@ -227,6 +255,8 @@ part_scatter_kernel(Cols cols, int32_t key_col, const int32_t* __restrict__ sel,
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem + stage_bytes + T * 12);     // 16 B
     int32_t* s_delta = reinterpret_cast<int32_t*>(smem + stage_bytes + T * 12 + 16);  // np1p
     int32_t* s_whist = s_delta + np1p;                                             // kWarps x np1
+    // partition ids from the histogram pass (T bytes), when it wrote them
+    uint8_t* s_pid = smem + ((stage_bytes + T * 12 + 16 + (np1p + kWarps * np1) * 4 + 15) & ~15u);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int64_t tile = blockIdx.x;
@@ -254,10 +284,11 @@ part_scatter_kernel(Cols cols, int32_t key_col, const int32_t* __restrict__ sel,
         }
         __syncthreads();
         if (tid == 0) {
-            mbar_arrive_expect_tx(bar, static_cast<uint32_t>(T) * row_bytes);
+            mbar_arrive_expect_tx(bar, static_cast<uint32_t>(T) * (row_bytes + (pid_in ? 1 : 0)));
             for (int c = 0; c < cols.ncols; ++c)
                 bulk_g2s(stage + cols.stage_off[c], static_cast<const char*>(cols.in[c]) + tbase * cols.width[c],
                          static_cast<uint32_t>(T * cols.width[c]), bar);
+            if (pid_in) bulk_g2s(s_pid, pid_in + tbase, static_cast<uint32_t>(T), bar);
         }
         if (!mbar_wait(bar, 0) && lane == 0) set_status(status, PX_ERR_TIMEOUT);
     } else {
@@ -273,6 +304,8 @@ part_scatter_kernel(Cols cols, int32_t key_col, const int32_t* __restrict__ sel,
                 stage_plain<int8_t, ITEMS>(static_cast<const int8_t*>(cols.in[c]), reinterpret_cast<int8_t*>(st), sel,
                                            tbase, tile_rows, warp, lane);
         }
+        if (pid_in)  // ids are stored by position, not through the selection
+            stage_plain<uint8_t, ITEMS>(pid_in, s_pid, nullptr, tbase, tile_rows, warp, lane);
         __syncthreads();
     }
 
@@ -288,7 +321,8 @@ part_scatter_kernel(Cols cols, int32_t key_col, const int32_t* __restrict__ sel,
 #pragma unroll
         for (int i = 0; i < ITEMS; ++i) {
             const int lp = local_pos<ITEMS>(warp, i, lane);
-            pidv[i] = FT || lp < tile_rows ? part_of(keys[lp], seed, nparts) : nparts;
+            pidv[i] = FT || lp < tile_rows ? (pid_in ? static_cast<uint32_t>(s_pid[lp]) : part_of(keys[lp], seed, nparts))
+                                           : nparts;
         }
         int32_t* wh = s_whist + warp * np1;
         const uint32_t lt = lanemask_lt();
@@ -394,7 +428,7 @@ size_t scatter_smem_bytes(int items, uint32_t stage_bytes, int32_t nparts) {
     const size_t T = static_cast<size_t>(kThreads) * items;
     const size_t np1 = static_cast<size_t>(nparts) + 1;
     const size_t np1p = (np1 + 3) & ~static_cast<size_t>(3);
-    return stage_bytes + T * 12 + 16 + np1p * 4 + kWarps * np1 * 4;
+    return align_up(stage_bytes + T * 12 + 16 + np1p * 4 + kWarps * np1 * 4, size_t(16)) + T;  // + ids
 }
 
 // Workspace: count matrix, offset matrix (partition-major, P x tiles int32) and the
@@ -404,6 +438,7 @@ struct PartScratch {
     int32_t* offs;
     void* scan;
     size_t scan_bytes;
+    uint8_t* pid;  // one partition id per position (nparts <= 256), or null
 };
 
 size_t part_mat_bytes(int64_t nrows, int32_t nparts) {
@@ -418,6 +453,7 @@ PartScratch part_scratch(void* d_ws, int64_t nrows, int64_t ntiles, int32_t npar
     p.offs = reinterpret_cast<int32_t*>(base + mat);
     p.scan = base + 2 * mat;
     p.scan_bytes = scan_scratch_bytes(cdiv(ntiles * nparts, kScanTile));
+    p.pid = nparts <= kPidMaxParts ? reinterpret_cast<uint8_t*>(base + 2 * mat + p.scan_bytes) : nullptr;
     return p;
 }
 
@@ -432,7 +468,7 @@ px_status launch_partition(const Cols& cols, int32_t key_col, const int32_t* d_s
     px_status s;
     const int64_t* key = static_cast<const int64_t*>(cols.in[key_col]);
     part_hist_kernel<ITEMS><<<static_cast<unsigned>(ntiles), kThreads, kWarps * nparts * sizeof(int32_t), st>>>(
-        key, d_sel, d_n, ncap, seed, static_cast<uint32_t>(nparts), ps.cnt, ntiles);
+        key, d_sel, d_n, ncap, seed, static_cast<uint32_t>(nparts), ps.cnt, ntiles, ps.pid);
     note_launch();
     if ((s = check_launch("px_partition hist")) != PX_OK) return s;
 
@@ -461,7 +497,7 @@ px_status launch_partition(const Cols& cols, int32_t key_col, const int32_t* d_s
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
         kern<<<static_cast<unsigned>(ntiles), kThreads, smem, st>>>(cols, key_col, d_sel, d_n, ncap, seed,
                                                                      static_cast<uint32_t>(nparts), ps.offs, ntiles,
-                                                                     stage_bytes, row_bytes, status);
+                                                                     stage_bytes, row_bytes, ps.pid, status);
     };
     static_assert(PX_MAX_PARTS <= 1024, "partition ids need at most 10 bits");
     switch (nparts <= 1 ? 0 : 32 - __builtin_clz(static_cast<unsigned>(nparts - 1))) {
@@ -492,7 +528,8 @@ size_t px_partition_ws_bytes(int64_t nrows, int32_t nparts) {
     if (nrows < 0) nrows = 0;
     if (nparts < 1) nparts = 1;
     const int64_t max_tiles = cdiv(nrows, kThreads * 2);
-    return kWsScratch + 2 * part_mat_bytes(nrows, nparts) + scan_scratch_bytes(cdiv(max_tiles * nparts, kScanTile));
+    return kWsScratch + 2 * part_mat_bytes(nrows, nparts) + scan_scratch_bytes(cdiv(max_tiles * nparts, kScanTile)) +
+           (nparts <= kPidMaxParts ? align_up(static_cast<size_t>(nrows), 256) : 0);
 }
 
 px_status px_partition_tuned(const px_batch* in, int32_t key_col, const int32_t* d_sel, const int64_t* d_nsel,

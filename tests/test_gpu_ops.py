@@ -78,6 +78,22 @@ def test_partition_parity(px, P):
                 np.testing.assert_array_equal(host(a, n), b)
 
 
+@pytest.mark.parametrize("P", [3, 64, 1000])
+def test_partition_parity_long_count_rows(px, P):
+    # a count matrix of more than 4096 tiles per partition (several scan tiles per row)
+    g = pxdata.rng(220 + P)
+    n = 8_400_777
+    cols = _part_cols(g, n)
+    for d_n in [None, 8_390_001]:
+        kw = {} if d_n is None else {"d_nrows": dev(np.array([d_n], np.int64))}
+        m = n if d_n is None else d_n
+        out, off = px.px_partition([dev(c) for c in cols], 0, P, 5, **kw)
+        want, woff = oracle.partition([c[:m] for c in cols], 0, P, 5)
+        np.testing.assert_array_equal(host(off), woff)
+        for a, b in zip(out, want):
+            np.testing.assert_array_equal(host(a, m), b)
+
+
 def test_partition_with_selection_and_key_not_first(px):
     g = pxdata.rng(210)
     n = 70_001
