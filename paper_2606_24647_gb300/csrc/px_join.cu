@@ -419,18 +419,17 @@ probe_emit_kernel(TableView t, int32_t S, const int64_t* __restrict__ fk, const 
         prow[i] = valid ? (kSel ? sel[tb + lp[i]] : static_cast<int32_t>(tb + lp[i])) : 0;
     }
     // The join's common shape (one 8-byte carried column, one 4-byte payload column):
-    // the carried values and the payload gathers are issued now, so their latency
-    // overlaps the ranking and the block combine below.
+    // the carried values (every position's, without waiting for its match row) and
+    // the payload gathers are issued now, so their latency overlaps the ranking and
+    // the block combine below.
     const bool early = oc.ncarry == 1 && oc.npay == 1 && oc.carry_w[0] == 8 && oc.pay_w[0] == 4;
     int64_t cv[kItems];
     int32_t pv[kItems];
     if (early) {
 #pragma unroll
         for (int i = 0; i < kItems; ++i) {
-            if (mr[i] >= 0) {
-                cv[i] = static_cast<const int64_t*>(oc.carry_in[0])[prow[i]];
-                pv[i] = static_cast<const int32_t*>(oc.pay_in[0])[mr[i]];
-            }
+            if (lp[i] < rows) cv[i] = static_cast<const int64_t*>(oc.carry_in[0])[prow[i]];
+            if (mr[i] >= 0) pv[i] = static_cast<const int32_t*>(oc.pay_in[0])[mr[i]];
         }
     }
     const int64_t tile_base = tile_off[blockIdx.x];
