@@ -267,6 +267,34 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
         : "memory");
 }
 
+// ------------------------------------------- programmatic dependent launch --
+// A kernel launched with launch_after() may start while the kernel before it on the
+// stream is still running (once every block of that one has called
+// allow_dependents() or exited); it must call wait_prior() before it reads anything
+// that kernel writes. Work that needs no such data (staging inputs of earlier
+// calls, clearing shared memory) runs before the wait and overlaps the tail of the
+// kernel before. wait_prior() returns when the kernel before has completed and its
+// memory is visible; since that kernel waited for its own predecessor the same way,
+// the whole stream before is then complete.
+__device__ __forceinline__ void wait_prior() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void allow_dependents() { asm volatile("griddepcontrol.launch_dependents;" :::); }
+
+template <typename... Params, typename... Args>
+cudaError_t launch_after(void (*kernel)(Params...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                         Args&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<Params>(args)...);
+}
+
 // ------------------------------------------------------------ reductions --
 // Fire-and-forget reductions (PTX red): no old value comes back, so the issuing
 // warp never waits on the memory system for them.

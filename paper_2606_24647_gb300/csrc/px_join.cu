@@ -22,6 +22,7 @@ namespace {
 
 __global__ void build_init_kernel(TableView t, int32_t S, int32_t unique, const int64_t* __restrict__ d_seg,
                                   const int64_t* __restrict__ d_n, int64_t ncap, const void* pay, int32_t pay_w) {
+    allow_dependents();  // the insert may launch; it waits for this grid before touching the table
     const int64_t n = actual_rows(d_n, ncap);
     const int64_t gtid = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
     const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
@@ -57,7 +58,8 @@ __global__ void build_insert_kernel(TableView t, int32_t S, int32_t unique, cons
     const int64_t n = actual_rows(d_n, ncap);
     const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const int64_t key = pk[i];
+    const int64_t key = pk[i];  // an input of earlier calls: loaded while the clearing finishes
+    wait_prior();               // the cleared buckets and the table's segment offsets
     if (key == kEmpty) {
         set_status(status, PX_ERR_UNSUPPORTED);
         return;
@@ -354,6 +356,8 @@ probe_scan_kernel(const int32_t* __restrict__ cnt, int64_t* __restrict__ off, in
     __shared__ int64_t s_tile;
     __shared__ int64_t s_warp[kScanThreads / 32];
     __shared__ int64_t s_excl;
+    wait_prior();        // the match kernel's tile counts
+    allow_dependents();  // the emit may launch and start its own loads
     const int64_t tile = next_tile(scan.counter, &s_tile);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t base = tile * kScanTile + static_cast<int64_t>(tid) * kScanItems;
@@ -414,23 +418,28 @@ probe_emit_kernel(TableView t, int32_t S, const int64_t* __restrict__ fk, const 
 #pragma unroll
     for (int i = 0; i < kItems; ++i) {
         lp[i] = warp * (32 * kItems) + i * 32 + lane;
-        const bool valid = lp[i] < rows;
-        mr[i] = valid ? mrow[tb + lp[i]] : kNoMatch;
-        prow[i] = valid ? (kSel ? sel[tb + lp[i]] : static_cast<int32_t>(tb + lp[i])) : 0;
+        prow[i] = lp[i] < rows ? (kSel ? sel[tb + lp[i]] : static_cast<int32_t>(tb + lp[i])) : 0;
     }
     // The join's common shape (one 8-byte carried column, one 4-byte payload column):
-    // the carried values (every position's, without waiting for its match row) and
-    // the payload gathers are issued now, so their latency overlaps the ranking and
-    // the block combine below.
+    // every position's carried value is loaded first (an input of earlier calls, so
+    // before the wait for the scan: it overlaps the scan's tail), then the match rows
+    // and the payload gathers, whose latency overlaps the ranking and block combine.
     const bool early = oc.ncarry == 1 && oc.npay == 1 && oc.carry_w[0] == 8 && oc.pay_w[0] == 4;
     int64_t cv[kItems];
     int32_t pv[kItems];
     if (early) {
 #pragma unroll
-        for (int i = 0; i < kItems; ++i) {
+        for (int i = 0; i < kItems; ++i)
             if (lp[i] < rows) cv[i] = static_cast<const int64_t*>(oc.carry_in[0])[prow[i]];
+    }
+    wait_prior();  // the scan's tile offsets, and the match rows and counts before them
+    allow_dependents();
+#pragma unroll
+    for (int i = 0; i < kItems; ++i) mr[i] = lp[i] < rows ? mrow[tb + lp[i]] : kNoMatch;
+    if (early) {
+#pragma unroll
+        for (int i = 0; i < kItems; ++i)
             if (mr[i] >= 0) pv[i] = static_cast<const int32_t*>(oc.pay_in[0])[mr[i]];
-        }
     }
     const int64_t tile_base = tile_off[blockIdx.x];
     int64_t pos[kItems];
@@ -550,6 +559,7 @@ probe_seg_kernel(TableView t, int32_t S, int32_t segmented, const int64_t* __res
                  int64_t ncap, const int32_t* __restrict__ mrow, const int64_t* __restrict__ tile_off,
                  const int64_t* __restrict__ d_nout, int64_t* __restrict__ d_out_seg) {
     __shared__ int32_t s_warp[kTile / 32];
+    wait_prior();  // the match rows, tile offsets and row count
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t q = blockIdx.x;
     const int64_t n = actual_rows(d_n, ncap);
@@ -661,9 +671,9 @@ px_status px_join_build(const px_batch* build, int32_t pk_col, const int64_t* d_
     note_launch();
     if ((s = check_launch("px_join_build init")) != PX_OK) return s;
     if (ncap > 0) {
-        build_insert_kernel<<<static_cast<unsigned>(cdiv(ncap, threads)), threads, 0, st>>>(
-            t, S, unique ? 1 : 0, static_cast<const int64_t*>(build->cols[pk_col].data), build->d_nrows, ncap, pay,
-            pay_w, &static_cast<WsHeader*>(d_ws)->status);
+        launch_after(build_insert_kernel, dim3(static_cast<unsigned>(cdiv(ncap, threads))), dim3(threads), 0, st, t, S,
+                     unique ? 1 : 0, static_cast<const int64_t*>(build->cols[pk_col].data), build->d_nrows, ncap,
+                     pay, pay_w, &static_cast<WsHeader*>(d_ws)->status);
         note_launch();
         if ((s = check_launch("px_join_build insert")) != PX_OK) return s;
     }
@@ -740,6 +750,7 @@ px_status px_join_probe(const void* d_table, const px_batch* probe, int32_t fk_c
     const int64_t* fk = static_cast<const int64_t*>(probe->cols[fk_col].data);
     const unsigned grid = static_cast<unsigned>(L.ntiles);
     cudaMemsetAsync(tcnt, 0, 4 * static_cast<size_t>(L.ntiles), st);
+    cudaMemsetAsync(ws + L.scan, 0, scan_scratch_bytes(L.nscan), st);  // before the match: the scan follows it directly
     const bool has_sel = d_sel != nullptr;
     const auto match = has_sel ? probe_match_kernel<true> : probe_match_kernel<false>;
     int per_sm = 0;
@@ -749,19 +760,18 @@ px_status px_join_probe(const void* d_table, const px_batch* probe, int32_t fk_c
                                            build_payload ? build_payload->nrows : 0, static_cast<uint32_t>(L.ntiles));
     note_launch();
     if ((s = check_launch("px_join_probe match")) != PX_OK) return s;
-    cudaMemsetAsync(ws + L.scan, 0, scan_scratch_bytes(L.nscan), st);
-    probe_scan_kernel<<<static_cast<unsigned>(L.nscan), kScanThreads, 0, st>>>(
-        tcnt, toff, L.ntiles, out->nrows, d_nout, scan_scratch(ws + L.scan), status, L.nscan);
+    launch_after(probe_scan_kernel, dim3(static_cast<unsigned>(L.nscan)), dim3(kScanThreads), 0, st, tcnt, toff,
+                 L.ntiles, out->nrows, d_nout, scan_scratch(ws + L.scan), status, L.nscan);
     note_launch();
     if ((s = check_launch("px_join_probe scan")) != PX_OK) return s;
     const auto emit = has_sel ? probe_emit_kernel<true> : probe_emit_kernel<false>;
-    emit<<<grid, kThreads, 0, st>>>(t, S, fk, d_sel, d_n, ncap, d_seg, mrow, tcnt, toff, oc, d_probe_row,
-                                    d_build_row, out->nrows);
+    launch_after(emit, dim3(grid), dim3(kThreads), 0, st, t, S, fk, d_sel, d_n, ncap, d_seg, mrow, tcnt, toff, oc,
+                 d_probe_row, d_build_row, out->nrows);
     note_launch();
     if ((s = check_launch("px_join_probe emit")) != PX_OK) return s;
     if (d_out_seg) {
-        probe_seg_kernel<<<static_cast<unsigned>(S + 1), kTile, 0, st>>>(t, S, nsegs > 0 ? 1 : 0, d_seg, fk, d_sel,
-                                                                          d_n, ncap, mrow, toff, d_nout, d_out_seg);
+        launch_after(probe_seg_kernel, dim3(static_cast<unsigned>(S + 1)), dim3(kTile), 0, st, t, S, nsegs > 0 ? 1 : 0,
+                     d_seg, fk, d_sel, d_n, ncap, mrow, toff, d_nout, d_out_seg);
         note_launch();
         if ((s = check_launch("px_join_probe segments")) != PX_OK) return s;
     }

@@ -71,6 +71,7 @@ part_hist_kernel(const int64_t* __restrict__ key, const int32_t* __restrict__ se
                  int32_t* __restrict__ cnt, int64_t ntiles, uint8_t* __restrict__ pid_out) {
     constexpr int T = kThreads * ITEMS;
     extern __shared__ int32_t s_hist[];  // [kWarps][nparts]
+    allow_dependents();  // the scan may launch now; it waits for this grid's counts
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     for (uint32_t q = tid; q < kWarps * nparts; q += kThreads) s_hist[q] = 0;
     const int64_t n = actual_rows(d_nsel, ncap);
@@ -128,6 +129,8 @@ part_scan_kernel(const int32_t* __restrict__ cnt, int32_t* __restrict__ offs, in
     __shared__ int64_t s_tile;
     __shared__ int32_t s_warp[33];
     __shared__ int64_t s_excl;
+    wait_prior();        // the histogram's counts (and its partition ids) are complete
+    allow_dependents();  // so the scatter, launched from here on, may read those ids at once
     const int64_t tile = next_tile(scan.counter, &s_tile);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t base = tile * kScanTile + static_cast<int64_t>(tid) * kScanItems;
@@ -265,17 +268,11 @@ part_scatter_kernel(Cols cols, int32_t key_col, const int32_t* __restrict__ sel,
     const int64_t rem = n - tbase;
     const int tile_rows = rem <= 0 ? 0 : (rem < T ? static_cast<int>(rem) : T);
     for (int k = tid; k < kWarps * np1; k += kThreads) s_whist[k] = 0;
-    // This tile's output start in each partition (one strided load per partition),
-    // requested now so its latency hides behind the staging of the tile.
-    int32_t my_off[kOffRegs];
-#pragma unroll
-    for (int r = 0; r < kOffRegs; ++r) {
-        const int q = tid + r * kThreads;
-        my_off[r] = q < static_cast<int>(nparts) ? offs[static_cast<int64_t>(q) * ntiles + tile] : 0;
-    }
 
     // Stage the tile of every column: TMA bulk copies for a full contiguous tile,
-    // plain loads for a gather through a selection or a ragged last tile.
+    // plain loads for a gather through a selection or a ragged last tile. The
+    // columns are inputs of earlier calls: their copies start before the wait for
+    // the scan (this kernel may be running while the scan finishes).
     const bool bulk = sel == nullptr && tile_rows == T;
     if (bulk) {
         if (tid == 0) {
@@ -288,8 +285,19 @@ part_scatter_kernel(Cols cols, int32_t key_col, const int32_t* __restrict__ sel,
             for (int c = 0; c < cols.ncols; ++c)
                 bulk_g2s(stage + cols.stage_off[c], static_cast<const char*>(cols.in[c]) + tbase * cols.width[c],
                          static_cast<uint32_t>(T * cols.width[c]), bar);
-            if (pid_in) bulk_g2s(s_pid, pid_in + tbase, static_cast<uint32_t>(T), bar);
         }
+    }
+    wait_prior();  // the scan's offsets, and the histogram's ids before it
+    // This tile's output start in each partition (one strided load per partition),
+    // requested now so its latency hides behind the staging of the tile.
+    int32_t my_off[kOffRegs];
+#pragma unroll
+    for (int r = 0; r < kOffRegs; ++r) {
+        const int q = tid + r * kThreads;
+        my_off[r] = q < static_cast<int>(nparts) ? offs[static_cast<int64_t>(q) * ntiles + tile] : 0;
+    }
+    if (bulk) {
+        if (tid == 0 && pid_in) bulk_g2s(s_pid, pid_in + tbase, static_cast<uint32_t>(T), bar);
         if (!mbar_wait(bar, 0) && lane == 0) set_status(status, PX_ERR_TIMEOUT);
     } else {
         for (int c = 0; c < cols.ncols; ++c) {
@@ -467,6 +475,7 @@ px_status launch_partition(const Cols& cols, int32_t key_col, const int32_t* d_s
                            cudaStream_t st) {
     px_status s;
     const int64_t* key = static_cast<const int64_t*>(cols.in[key_col]);
+    cudaMemsetAsync(ps.scan, 0, ps.scan_bytes, st);  // before the histogram: the scan launches right after it
     part_hist_kernel<ITEMS><<<static_cast<unsigned>(ntiles), kThreads, kWarps * nparts * sizeof(int32_t), st>>>(
         key, d_sel, d_n, ncap, seed, static_cast<uint32_t>(nparts), ps.cnt, ntiles, ps.pid);
     note_launch();
@@ -474,10 +483,8 @@ px_status launch_partition(const Cols& cols, int32_t key_col, const int32_t* d_s
 
     const int64_t total = ntiles * nparts;
     const int64_t nscan = cdiv(total, kScanTile);
-    cudaMemsetAsync(ps.scan, 0, ps.scan_bytes, st);
-    part_scan_kernel<<<static_cast<unsigned>(nscan), kScanThreads, 0, st>>>(
-        ps.cnt, ps.offs, total, ntiles, static_cast<uint32_t>(nparts), d_offsets, scan_scratch(ps.scan), status,
-        nscan);
+    launch_after(part_scan_kernel, dim3(static_cast<unsigned>(nscan)), dim3(kScanThreads), 0, st, ps.cnt, ps.offs, total,
+                 ntiles, static_cast<uint32_t>(nparts), d_offsets, scan_scratch(ps.scan), status, nscan);
     note_launch();
     if ((s = check_launch("px_partition scan")) != PX_OK) return s;
 
@@ -495,9 +502,9 @@ px_status launch_partition(const Cols& cols, int32_t key_col, const int32_t* d_s
     }
     auto go = [&](auto kern) {
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
-        kern<<<static_cast<unsigned>(ntiles), kThreads, smem, st>>>(cols, key_col, d_sel, d_n, ncap, seed,
-                                                                     static_cast<uint32_t>(nparts), ps.offs, ntiles,
-                                                                     stage_bytes, row_bytes, ps.pid, status);
+        launch_after(kern, dim3(static_cast<unsigned>(ntiles)), dim3(kThreads), smem, st, cols, key_col, d_sel, d_n,
+                     ncap, seed, static_cast<uint32_t>(nparts), ps.offs, ntiles, stage_bytes, row_bytes, ps.pid,
+                     status);
     };
     static_assert(PX_MAX_PARTS <= 1024, "partition ids need at most 10 bits");
     switch (nparts <= 1 ? 0 : 32 - __builtin_clz(static_cast<unsigned>(nparts - 1))) {
