@@ -237,7 +237,7 @@ __device__ __forceinline__ int32_t walk_on(const Bucket* segb, uint32_t nb, uint
 // only in warps where some lane needs it. Only positions below the row count are
 // written: the emit reads no other.
 template <bool kSel>
-__global__ void __launch_bounds__(kMatchThreads, 2)
+__global__ void __launch_bounds__(kMatchThreads, 3)
 probe_match_kernel(TableView t, int32_t S, const int64_t* __restrict__ fk, const int32_t* __restrict__ sel,
                    const int64_t* __restrict__ d_n, int64_t ncap, const int64_t* __restrict__ pseg,
                    int32_t* __restrict__ mrow, int32_t* __restrict__ tile_cnt, int32_t* status, int32_t npay,
