@@ -857,6 +857,180 @@ px_status launch_sum_count(const Spec& sp, int32_t sum_slot, int32_t cnt_slot, c
     return check_launch("px_groupby_agg sum-count");
 }
 
+// px_join_probe_agg's SUM + COUNT shape with the lean kernel's accumulation:
+// every position's key is looked up in its segment of the join table (one sector:
+// keys, build rows and the group column copied beside them; a walk on for the
+// keys displaced past their home bucket), its group's dense slot comes from the
+// copied value (else from a gather of the group column), and its amount is added
+// to the block's slot as in groupby_sum_count_kernel. The joined rows are never
+// written. Two positions per thread (one 16-byte load of their keys).
+template <typename VT>
+__global__ void __launch_bounds__(kThreads, 1)
+groupby_probe_sum_count_kernel(Spec sp, int32_t sum_slot, int32_t cnt_slot, const int64_t* __restrict__ d_n,
+                               int64_t ncap, const int64_t* __restrict__ d_seg, GTable g, int64_t max_groups,
+                               int32_t* __restrict__ out_seg, int32_t* status) {
+    constexpr int ITEMS = 2;
+    constexpr int T = kThreads * ITEMS;
+    extern __shared__ __align__(16) uint32_t s_acc[];  // low words [D], high words [D], counts [D]
+    const uint32_t D = sp.D;
+    uint32_t* s_lo = s_acc;
+    uint32_t* s_hi = s_acc + D;
+    uint32_t* s_cnt = s_acc + 2 * static_cast<size_t>(D);
+    const int tid = threadIdx.x, lane = tid & 31;
+    for (uint32_t w = tid; w < 3 * D; w += kThreads) s_acc[w] = 0;
+    __syncthreads();
+    const TableHeader* h = sp.probe_t.hdr;
+    const int S = sp.nsegs > 0 ? sp.nsegs : 1;
+    if (h->magic != kMagic || h->nsegs != S || h->unique == 0 || h->nbuild > sp.nbuild) {  // unusable table
+        if (blockIdx.x == 0 && tid == 0)
+            set_status(status, h->magic == kMagic && h->unique == 0 ? PX_ERR_UNSUPPORTED : PX_ERR_INVALID);
+        return;
+    }
+    const bool group_in_table = h->pay_src == sp.group_col && h->pay_w == sp.group_w;
+    const int64_t* __restrict__ fk = sp.probe_fk;
+    const VT* __restrict__ val = static_cast<const VT*>(sp.a_in[sum_slot]);
+    const int64_t lo = sp.lo[0];
+    const int64_t n = actual_rows(d_n, ncap);
+    const int64_t chunk = cdiv(cdiv(n, gridDim.x), T) * T;
+    const int64_t cb = static_cast<int64_t>(blockIdx.x) * chunk;
+    const int64_t ce = n < cb + chunk ? n : cb + chunk;
+    // The keys and amounts of the next tile to visit are loaded while the current
+    // tile's buckets are in flight (one memory round trip per tile, not two).
+    auto load_tile = [&](int64_t tb, int64_t* k, VT* v) {
+        const int64_t r0 = tb + static_cast<int64_t>(tid) * ITEMS;
+        if (r0 + ITEMS <= ncap) {
+            const longlong2 k2 = *reinterpret_cast<const longlong2*>(fk + r0);
+            k[0] = k2.x;
+            k[1] = k2.y;
+#pragma unroll
+            for (int i = 0; i < ITEMS; ++i) v[i] = val[r0 + i];
+        } else {
+#pragma unroll
+            for (int i = 0; i < ITEMS; ++i) {
+                k[i] = r0 + i < ncap ? fk[r0 + i] : kEmpty;
+                v[i] = r0 + i < ncap ? val[r0 + i] : VT(0);
+            }
+        }
+    };
+    int64_t kn[ITEMS];
+    VT vn[ITEMS];
+    if (cb < ce) load_tile(cb, kn, vn);
+    int64_t pos = cb;
+    while (pos < ce) {
+        int q = 0;
+        int64_t qend = ce;
+        if (sp.nsegs > 1) {
+            q = seg_of(d_seg, sp.nsegs, pos);
+            if (q + 1 < sp.nsegs) {
+                const int64_t e = d_seg[q + 1];
+                if (e > pos && e < ce) qend = e;
+            }
+        }
+        const SegGeom geo = seg_geom(sp.probe_t, q);
+        const Bucket* const segb = sp.probe_t.bk + geo.b0;
+        for (int64_t tb = pos / T * T; tb < qend; tb += T) {
+            const int64_t r0 = tb + static_cast<int64_t>(tid) * ITEMS;
+            int64_t k[ITEMS];
+            VT v[ITEMS];
+#pragma unroll
+            for (int i = 0; i < ITEMS; ++i) {
+                k[i] = kn[i];
+                v[i] = vn[i];
+            }
+            bool live[ITEMS];
+            uint32_t hb[ITEMS];
+            BucketRegs bv[ITEMS];
+#pragma unroll
+            for (int i = 0; i < ITEMS; ++i) {
+                const int64_t r = r0 + i;
+                live[i] = r >= pos && r < qend && k[i] != kEmpty;
+                hb[i] = home_bucket(static_cast<uint64_t>(k[i]), geo.nb);
+                bv[i] = load_bucket(segb + hb[i]);  // hb < nb: inside the segment
+            }
+            // next visit: this segment's next tile, or the tile where the next segment starts
+            const int64_t nxt = tb + T < qend ? tb + T : (qend < ce ? qend / T * T : -1);
+            if (nxt >= 0) load_tile(nxt, kn, vn);
+            uint32_t idx[ITEMS];
+            int64_t gk[ITEMS];
+#pragma unroll
+            for (int i = 0; i < ITEMS; ++i) {
+                idx[i] = kIdxNone;
+                gk[i] = 0;
+                if (!live[i]) continue;
+                bool end;
+                int l = bucket_find(bv[i], k[i], &end);
+                if (l < 0 && !end) l = walk_find(segb, geo.nb, hb[i], k[i], &bv[i]);
+                if (l < 0) continue;  // no match: no group
+                gk[i] = group_in_table ? static_cast<int64_t>(bucket_pay(bv[i], l))
+                                       : load_int(sp.group_col, sp.group_w, bucket_row(bv[i], l));
+                const uint64_t o = static_cast<uint64_t>(gk[i] - lo);
+                idx[i] = o < D ? static_cast<uint32_t>(o) : kIdxOutside;
+            }
+#pragma unroll
+            for (int i = 0; i < ITEMS; ++i) {
+                const uint32_t c0 = __shfl_sync(FULL, idx[i], 0);
+                const uint32_t mm = __ballot_sync(FULL, idx[i] == c0);
+                uint64_t x = static_cast<uint64_t>(static_cast<int64_t>(v[i]));
+                uint32_t cnt = 1;
+                uint32_t d = idx[i];
+                if (c0 < kIdxOutside && __popc(mm) >= kMajority) {  // warp-uniform
+                    // Lane 0 (always in the group) applies the group's totals; the
+                    // group's other lanes drop out; lanes outside it keep their row.
+                    const bool in = (mm >> lane) & 1u;
+                    const uint64_t total = warp_sum_u64(in ? x : 0);
+                    if (lane == 0) {
+                        x = total;
+                        cnt = __popc(mm);
+                    } else if (in) {
+                        d = kIdxNone;
+                    }
+                }
+                if (d < kIdxOutside) {
+                    const uint32_t xl = static_cast<uint32_t>(x);
+                    const uint32_t old = atomicAdd(&s_lo[d], xl);
+                    const uint32_t hi = static_cast<uint32_t>(x >> 32) + (old + xl < old ? 1u : 0u);
+                    if (hi) red_add_shared(&s_hi[d], hi);
+                    red_add_shared(&s_cnt[d], cnt);
+                } else if (d == kIdxOutside) {
+                    uint64_t full[2];
+                    full[sum_slot] = x;
+                    full[cnt_slot] = 1;
+                    global_add(g, sp, compose(sp, gk[i], 0, q), full, max_groups, out_seg, status);
+                }
+            }
+        }
+        // Segment q's slots into the dense global array, then cleared for the next.
+        __syncthreads();
+        const uint64_t ebase = static_cast<uint64_t>(q) * D;
+        for (uint32_t d = tid; d < D; d += kThreads) {
+            const uint32_t c = s_cnt[d];
+            if (c) {
+                red_add_global(&sp.dg_acc[sum_slot * sp.E + ebase + d],
+                               (static_cast<unsigned long long>(s_hi[d]) << 32) | s_lo[d]);
+                red_add_global(&sp.dg_acc[cnt_slot * sp.E + ebase + d], c);
+                s_lo[d] = s_hi[d] = s_cnt[d] = 0;
+            }
+        }
+        __syncthreads();
+        pos = qend;
+    }
+}
+
+template <typename VT>
+px_status launch_probe_sum_count(const Spec& sp, int32_t sum_slot, int32_t cnt_slot, const int64_t* d_n, int64_t ncap,
+                                 const int64_t* d_seg, const GTable& g, int64_t max_groups, int32_t* out_seg,
+                                 int32_t* status, cudaStream_t st) {
+    auto kernel = groupby_probe_sum_count_kernel<VT>;
+    const size_t smem = 12 * static_cast<size_t>(sp.D);
+    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    const int64_t grid = std::max<int64_t>(
+        1, std::min<int64_t>(cdiv(ncap, std::max<int64_t>(kThreads * 2, 4 * static_cast<int64_t>(sp.D))), sm_count()));
+    kernel<<<static_cast<unsigned>(grid), kThreads, smem, st>>>(sp, sum_slot, cnt_slot, d_n, ncap, d_seg, g,
+                                                              max_groups, out_seg, status);
+    note_launch();
+    return check_launch("px_join_probe_agg sum-count");
+}
+
 constexpr int kEmitThreads = 256;
 constexpr int kEmitItems = 8;
 constexpr int kEmitTile = kEmitThreads * kEmitItems;
@@ -1228,7 +1402,19 @@ static px_status groupby_impl(const px_batch* in, const int32_t* key_cols, int32
     const bool sum_count = ncap > 0 && !probe && sp.dense && !sp.direct && sp.dglobal && sp.reps == 1 &&
                            d_sel == nullptr && nkeys == 1 && (sp.key_w[0] == 4 || sp.key_w[0] == 8) &&
                            sum_slot >= 0 && cnt_slot >= 0 && 12 * static_cast<size_t>(sp.D) <= kSmemBudget;
-    if (sum_count) {
+    // The same shape fed by the join probe, with the rows' keys looked up in the table.
+    const bool probe_sum_count = ncap > 0 && probe && sp.dense && !sp.direct && sp.dglobal && sp.reps == 1 &&
+                                 d_sel == nullptr && nkeys == 1 && sum_slot >= 0 && cnt_slot >= 0 &&
+                                 12 * static_cast<size_t>(sp.D) <= kSmemBudget;
+    if (probe_sum_count) {
+        const int64_t* d_n = in->d_nrows;
+        s = sp.a_w[sum_slot] == 8
+                ? launch_probe_sum_count<int64_t>(sp, sum_slot, cnt_slot, d_n, ncap, d_seg, g, max_groups, d_out_seg,
+                                                  status, st)
+                : launch_probe_sum_count<int32_t>(sp, sum_slot, cnt_slot, d_n, ncap, d_seg, g, max_groups, d_out_seg,
+                                                  status, st);
+        if (s != PX_OK) return s;
+    } else if (sum_count) {
         const int64_t* d_n = in->d_nrows;
         if (sp.key_w[0] == 4 && sp.a_w[sum_slot] == 8)
             s = launch_sum_count<int32_t, int64_t>(sp, sum_slot, cnt_slot, d_n, ncap, d_seg, g, max_groups, d_out_seg,

@@ -32,22 +32,24 @@ def test_probe_agg_segmented_partial_matches_oracle(px):
     assert n == count(r["final"]["ngroups"])
 
 
+@pytest.mark.parametrize("use_sel", [True, False])
 @pytest.mark.parametrize("in_table", [False, True])
 @pytest.mark.parametrize("rng", ["exact", "narrow"])
-def test_probe_agg_single_with_selection_and_misses(px, rng, in_table):
+def test_probe_agg_single_with_selection_and_misses(px, rng, in_table, use_sel):
+    # without a selection, SUM + COUNT runs through the lean probe-fed kernel
     d = pxdata.plain_join(20_000, 300_003, nattr=25)
     g = pxdata.rng(900)
     d["fk"][::11] = g.integers(20_001, 30_000, size=d["fk"][::11].size)  # keys with no match
-    sel = oracle.filter(d["date"], pxdata.CFG2_DATE_LO, pxdata.CFG2_DATE_HI)
+    sel = oracle.filter(d["date"], pxdata.CFG2_DATE_LO, pxdata.CFG2_DATE_HI) if use_sel else None
     pr, br, _ = oracle.join(d["pk"], d["fk"], sel=sel)
     want = oracle.groupby([d["attr"][br]], [(oracle.SUM, d["amount"][pr], None), (oracle.COUNT, None, None)])
     dim = [dev(d["pk"]), dev(d["attr"])]
     # in_table: the group column is copied beside the keys and read from the table
     table = px.px_join_build(dim, 0, unique=True, pay_col=1 if in_table else None)
     lo, hi = (0, 24) if rng == "exact" else (5, 12)  # narrow: keys outside take the hash path
+    kw = {"sel": dev(sel), "nsel": dev(np.array([sel.size], np.int64))} if use_sel else {}
     res = px.px_join_probe_agg(table, [dev(d["fk"]), dev(d["amount"])], 0, dim[1], (lo, hi),
-                               [(px.PX_SUM, 1, None), (px.PX_COUNT, None, None)], max_groups=64,
-                               sel=dev(sel), nsel=dev(np.array([sel.size], np.int64)))
+                               [(px.PX_SUM, 1, None), (px.PX_COUNT, None, None)], max_groups=64, **kw)
     assert_groups_equal(res, want, 1)
 
 
