@@ -53,6 +53,21 @@ def test_probe_agg_single_with_selection_and_misses(px, rng, in_table, use_sel):
     assert_groups_equal(res, want, 1)
 
 
+def test_probe_agg_int8_group_copied_into_the_table(px):
+    # a one-byte group column copied beside the keys (sign-extended like the gather)
+    d = pxdata.plain_join(5_000, 200_001, nattr=25)
+    g = pxdata.rng(901)
+    grp = g.integers(-100, 100, size=d["pk"].size, dtype=np.int8)
+    pr, br, _ = oracle.join(d["pk"], d["fk"])
+    want = oracle.groupby([grp[br]], [(oracle.SUM, d["amount"][pr], None), (oracle.COUNT, None, None)])
+    dim = [dev(d["pk"]), dev(grp)]
+    for pay_col in (None, 1):
+        table = px.px_join_build(dim, 0, unique=True, pay_col=pay_col)
+        res = px.px_join_probe_agg(table, [dev(d["fk"]), dev(d["amount"])], 0, dim[1], (-100, 99),
+                                   [(px.PX_SUM, 1, None), (px.PX_COUNT, None, None)], max_groups=256)
+        assert_groups_equal(res, want, 1)
+
+
 def test_probe_agg_multimap_table_is_unsupported(px):
     pk = np.array([1, 1, 2, 3], np.int64)
     attr = np.array([0, 1, 2, 3], np.int32)
