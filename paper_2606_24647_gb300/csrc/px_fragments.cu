@@ -9,9 +9,11 @@
 // Work items are (fragment, chunk of rows), handed out by a device counter in
 // the order of decreasing fragment size. A block walks its chunk in tiles of
 // THREADS x ITEMS rows: per row the filter column, join key and aggregate inputs
-// load together, then the key's home bucket (one sector), then the build row,
-// then the group key gathered from the build column; the aggregates go into the
-// fragment's dense accumulators (group key - group_lo indexes them):
+// load together, then the key's home bucket (one sector: keys, build rows and,
+// when the dimension was built with its group column copied, the group keys),
+// else the group key gathered from the build column at the build row; the
+// aggregates go into the fragment's dense accumulators (group key - group_lo
+// indexes them):
 //   * shared mode (small key ranges): block arrays in shared memory, cleared per
 //     work item and added into the fragment's global arrays at its end;
 //   * direct mode: 64-bit reductions straight into the global arrays.

@@ -90,7 +90,8 @@ __global__ void build_insert_kernel(TableView t, int32_t S, int32_t unique, cons
 
 // ------------------------------------------------------------------ probe ----
 //
-// Three streaming launches, none of which waits on another block:
+// Three streaming launches (plus one for the segments' first output rows), none
+// of which waits on another block:
 //   match - per position, find the key's build row in its segment's table and
 //           record it (mrow: build row, -1 for no match, or -(slot + 2) for the
 //           first of several matches in a multi-map); per-tile match counts.
@@ -99,8 +100,9 @@ __global__ void build_insert_kernel(TableView t, int32_t S, int32_t unique, cons
 //           output row; carried probe columns and gathered payload columns are
 //           written column by column, every load of a column before its stores.
 // The extra 4 bytes written and read per position buy the removal of the
-// serialised look-back that stalled a single-pass probe behind two dependent
-// memory round trips (key, then table slot) per tile.
+// serialised look-back that stalled a single-pass probe: a block of a single
+// pass alternates latency-bound lookups and DRAM-bound emission behind its
+// barriers, while separate kernels each run at full occupancy.
 
 constexpr int kThreads = 256;
 constexpr int kItems = 4;
