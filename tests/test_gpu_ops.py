@@ -204,6 +204,27 @@ def test_join_table_at_a_16_byte_offset(px):
         np.testing.assert_array_equal(host(res["build_row"], m), br)
 
 
+@pytest.mark.parametrize("nb", [65_534, 65_535, 70_000])
+def test_join_around_two_to_the_16_build_rows(px, nb):
+    # unique tables of about 2^16 build rows, whole and cut into segments, with
+    # probes that mostly match and a tail of misses
+    g = pxdata.rng(311)
+    pk = (g.permutation(nb) * 3 + 1).astype(np.int64)
+    fk = np.concatenate([pk[g.integers(0, nb, 90_000)], pxdata.random_column(g, 20_001, np.int64, 0, 3 * nb)])
+    for seg in [None, np.array([0, 1000, nb // 2, nb], np.int64)]:
+        pseg = None if seg is None else np.array([0, 10_000, 60_000, fk.size], np.int64)
+        res, attr, amount, ws = _join(px, pk, fk, bseg=seg, pseg=pseg)
+        assert ws.status() == px.PX_OK
+        pr, br, oseg = oracle.join(pk, fk, build_seg=seg, probe_seg=pseg)
+        m = count(res["nout"])
+        assert m == pr.size
+        np.testing.assert_array_equal(host(res["probe_row"], m), pr)
+        np.testing.assert_array_equal(host(res["build_row"], m), br)
+        np.testing.assert_array_equal(host(res["cols"][1], m), attr[br])
+        if pseg is not None:
+            np.testing.assert_array_equal(host(res["out_seg"]), oseg)
+
+
 def test_join_multi_match_parity(px):
     g = pxdata.rng(302)
     pk = pxdata.random_column(g, 3000, np.int64, 0, 700)       # ~4 duplicates per key
